@@ -1,0 +1,218 @@
+"""Seeded synthetic earth models and tool layouts (shared by the oracle, the tests and the bench).
+
+This module only *describes inputs*: voxel grids, absolute conductivity tensors, magnetic-dipole
+sources and receiver positions. It contains none of the integral-equation arithmetic (no Green's
+functions, no operator, no solver), so the CPU oracle and the CUDA path can both consume it
+without sharing any of the method's code.
+
+Conventions (stated once, used everywhere):
+  * A grid is ``(nx, ny, nz, h, origin)``; ``origin`` is the minimum corner, cell centres sit at
+    ``origin + (i + 1/2) h`` and x varies fastest in memory (Section 2.2 of the paper: uniform
+    grid blocks with centroids r^j and volume h^3).
+  * The tool origin (0, 0, 0) is placed on a cell *vertex* so that transmitters and receivers at
+    multiples of h never coincide with a cell centre (where the scalar Green's function is
+    singular).
+  * Conductivity is the absolute tensor sigma (not the contrast), stored per voxel as the six
+    unique components ``(xx, yy, zz, xy, xz, yz)`` of the symmetric 3x3 tensor (Appendix C), array
+    shape ``(nz, ny, nx, 6)``, float64.
+  * Transversely isotropic layers are rotated into the tool frame by Appendix C: with the layer
+    normal n = (sin t cos p, sin t sin p, cos t) the rotated tensor is
+    ``sigma_h I + (sigma_v - sigma_h) n n^T``.
+
+The paper's own formations exist only in figures that are not available, so every workload here
+is a seeded stand-in with the shapes and value ranges of the paper's examples (Section 3).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+COMPONENTS6 = ("xx", "yy", "zz", "xy", "xz", "yz")
+
+
+@dataclass
+class Grid:
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    origin: tuple  # (x0, y0, z0): minimum corner of the voxel grid, metres
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def centres(self):
+        """Cell-centre coordinates as three 1-D arrays (x, y, z)."""
+        x = self.origin[0] + (np.arange(self.nx) + 0.5) * self.h
+        y = self.origin[1] + (np.arange(self.ny) + 0.5) * self.h
+        z = self.origin[2] + (np.arange(self.nz) + 0.5) * self.h
+        return x, y, z
+
+
+@dataclass
+class Dipole:
+    pos: tuple
+    moment: tuple  # magnetic moment, A m^2
+
+
+@dataclass
+class Workload:
+    name: str
+    grid: Grid
+    sigma0: float  # background conductivity, S/m
+    freq: float  # Hz
+    sigma6: np.ndarray  # (nz, ny, nx, 6) absolute conductivity
+    sources: list
+    receivers: np.ndarray  # (n_rx, 3)
+    z_split: list = field(default_factory=list)  # sub-domain boundaries along z (voxel index)
+    tol: float = 1e-6
+    restart: int = 30
+
+
+def centred_grid(nx: int, ny: int, nz: int, h: float) -> Grid:
+    """A grid whose centre is the tool origin (0,0,0), which then lies on a cell vertex (even n)."""
+    return Grid(nx, ny, nz, h, (-nx * h / 2.0, -ny * h / 2.0, -nz * h / 2.0))
+
+
+def ti_tensor(sigma_h, sigma_v, theta, phi):
+    """Transversely isotropic conductivity rotated into the tool frame (Appendix C).
+
+    Returns the six components (xx, yy, zz, xy, xz, yz) with a trailing axis of length 6.
+    """
+    sigma_h = np.asarray(sigma_h, dtype=np.float64)
+    sigma_v = np.asarray(sigma_v, dtype=np.float64)
+    nvec = (np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta))
+    d = sigma_v - sigma_h
+    out = np.empty(np.broadcast(sigma_h, sigma_v).shape + (6,))
+    out[..., 0] = sigma_h + d * nvec[0] * nvec[0]
+    out[..., 1] = sigma_h + d * nvec[1] * nvec[1]
+    out[..., 2] = sigma_h + d * nvec[2] * nvec[2]
+    out[..., 3] = d * nvec[0] * nvec[1]
+    out[..., 4] = d * nvec[0] * nvec[2]
+    out[..., 5] = d * nvec[1] * nvec[2]
+    return out
+
+
+def sigma6_to_matrix(s6: np.ndarray) -> np.ndarray:
+    """(…, 6) -> (…, 3, 3) symmetric tensor."""
+    m = np.empty(s6.shape[:-1] + (3, 3), dtype=s6.dtype)
+    m[..., 0, 0] = s6[..., 0]
+    m[..., 1, 1] = s6[..., 1]
+    m[..., 2, 2] = s6[..., 2]
+    m[..., 0, 1] = m[..., 1, 0] = s6[..., 3]
+    m[..., 0, 2] = m[..., 2, 0] = s6[..., 4]
+    m[..., 1, 2] = m[..., 2, 1] = s6[..., 5]
+    return m
+
+
+def _log_uniform(rng, lo_exp, hi_exp, size=None):
+    return 10.0 ** rng.uniform(lo_exp, hi_exp, size)
+
+
+def _random_rotation(rng) -> np.ndarray:
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def layered_vti(grid: Grid, seed: int, n_layers: int = 3, ratio_max: float = 5.0) -> np.ndarray:
+    """Horizontal VTI layers: interfaces at sorted seeded uniform z inside the grid's z-extent,
+    sigma_h log-uniform in [0.01, 10] S/m, anisotropy ratio r ~ U(1, ratio_max), sigma_v = sigma_h / r.
+    """
+    rng = np.random.default_rng(seed)
+    z0 = grid.origin[2]
+    z1 = z0 + grid.nz * grid.h
+    iface = np.sort(rng.uniform(z0, z1, n_layers - 1))
+    sh = _log_uniform(rng, -2.0, 1.0, n_layers)
+    ratio = rng.uniform(1.0, ratio_max, n_layers)
+    sv = sh / ratio
+    _, _, zc = grid.centres()
+    layer = np.searchsorted(iface, zc)  # (nz,)
+    s6 = np.zeros((grid.nz, grid.ny, grid.nx, 6))
+    s6[..., 0] = sh[layer][:, None, None]
+    s6[..., 1] = sh[layer][:, None, None]
+    s6[..., 2] = sv[layer][:, None, None]
+    return s6
+
+
+def dipping_ti_with_ellipsoids(grid: Grid, seed: int, n_layers: int = 5, ratio_max: float = 10.0,
+                               dip_max_deg: float = 30.0, n_ellipsoids: int = 2) -> np.ndarray:
+    """Dipping TI layers (common dip/azimuth, Appendix C rotation) plus isotropic ellipsoids."""
+    rng = np.random.default_rng(seed)
+    theta = np.deg2rad(rng.uniform(0.0, dip_max_deg))
+    phi = rng.uniform(0.0, 2.0 * np.pi)
+    nrm = np.array([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)])
+    xc, yc, zc = grid.centres()
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+    dist = X * nrm[0] + Y * nrm[1] + Z * nrm[2]
+    half = 0.5 * grid.h * np.array([grid.nx, grid.ny, grid.nz])
+    reach = float(np.abs(nrm) @ half)
+    iface = np.sort(rng.uniform(-0.8 * reach, 0.8 * reach, n_layers - 1))
+    sh = _log_uniform(rng, -2.0, 1.0, n_layers)
+    ratio = rng.uniform(1.0, ratio_max, n_layers)
+    sv = sh / ratio
+    layer = np.searchsorted(iface, dist)
+    s6 = ti_tensor(sh[layer], sv[layer], theta, phi)
+    lo = np.array(grid.origin)
+    ext = grid.h * np.array([grid.nx, grid.ny, grid.nz])
+    for _ in range(n_ellipsoids):
+        c = lo + ext * rng.uniform(0.1, 0.9, 3)
+        ax = rng.uniform(1.0, 4.0, 3)
+        rot = _random_rotation(rng)
+        sig = _log_uniform(rng, -2.0, 1.0)
+        d = np.stack([X - c[0], Y - c[1], Z - c[2]], axis=-1) @ rot  # body-frame coordinates
+        inside = np.sum((d / ax) ** 2, axis=-1) <= 1.0
+        s6[inside, :3] = sig
+        s6[inside, 3:] = 0.0
+    return s6
+
+
+def coaxial_tool(spacings=(0.5, 1.0, 2.0)):
+    """z-directed unit magnetic dipole at the origin, receivers on the tool (z) axis."""
+    src = [Dipole((0.0, 0.0, 0.0), (0.0, 0.0, 1.0))]
+    rx = np.array([[0.0, 0.0, s] for s in spacings], dtype=np.float64)
+    return src, rx
+
+
+def config1(seed: int = 0) -> Workload:
+    """Plain full-domain IE: 16^3 voxels of 0.5 m, 3 horizontal VTI layers (ratio 1-5),
+    coaxial z-dipole with receivers at 0.5/1/2 m, f = 100 kHz, sigma0 = 0.1 S/m, GMRES(30), tol 1e-8."""
+    g = centred_grid(16, 16, 16, 0.5)
+    src, rx = coaxial_tool()
+    return Workload("full-domain IE 16x16x16 @0.5 m, 3 VTI layers, 100 kHz", g, 0.1, 1.0e5,
+                    layered_vti(g, seed), src, rx, z_split=[0, 16], tol=1e-8, restart=30)
+
+
+def config2(seed: int = 0, scale: int = 1) -> Workload:
+    """Plain DD: 128x128x256 voxels of 0.25 m split into 2 sub-domains along z, 5 dipping TI layers
+    (ratio 1-10) plus 2 isotropic ellipsoids, coaxial z-dipole at the domain centre, f = 400 kHz,
+    sigma0 = 0.1 S/m, block Gauss-Seidel with adaptive tolerance, tol 1e-6.
+
+    ``scale`` > 1 divides every grid dimension (same physical cell size), giving the same kind of
+    model on a smaller box for tests.
+    """
+    nx, ny, nz = 128 // scale, 128 // scale, 256 // scale
+    g = centred_grid(nx, ny, nz, 0.25)
+    src, rx = coaxial_tool()
+    name = f"DD {nx}x{ny}x{nz} @0.25 m, 2 blocks GS-A, 5 dipping TI layers + 2 ellipsoids, 400 kHz"
+    return Workload(name, g, 0.1, 4.0e5, dipping_ti_with_ellipsoids(g, seed), src, rx,
+                    z_split=[0, nz // 2, nz], tol=1e-6, restart=30)
+
+
+def random_contrast_sigma6(shape, seed: int, sigma0: float, spread: float = 0.5) -> np.ndarray:
+    """Random symmetric positive-definite conductivity around sigma0 (for operator parity tests)."""
+    rng = np.random.default_rng(seed)
+    a = rng.normal(scale=spread, size=tuple(shape) + (3, 3))
+    m = sigma0 * (np.eye(3) + 0.5 * (a @ np.swapaxes(a, -1, -2)))
+    return np.stack([m[..., 0, 0], m[..., 1, 1], m[..., 2, 2], m[..., 0, 1], m[..., 0, 2],
+                     m[..., 1, 2]], axis=-1)
+
+
+def random_field(n3_shape, seed: int) -> np.ndarray:
+    """Random complex field of shape (3, nz, ny, nx)."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=n3_shape) + 1j * rng.normal(size=n3_shape)
