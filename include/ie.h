@@ -1,0 +1,179 @@
+/*
+ * ie.h — C ABI of the GB300 integral-equation (IE) forward model with domain decomposition.
+ *
+ * The library solves the discretised electric-field integral equation (eq. 8 of Saputera et al.,
+ * "3D induction log modelling with integral equation method and domain decomposition
+ * preconditioning"):
+ *
+ *     (I - G dsigma) E = E0,       dsigma = sigma - sigma0 I          (Section 2.1, eqs. 3, 8)
+ *
+ * on a uniform voxel grid embedded in a homogeneous isotropic background sigma0, for magnetic-dipole
+ * transmitters, and returns the total magnetic field H = H0 + H^s at receivers (eq. 4). G is the
+ * convolution with the electric Green's dyadic (eqs. 5, 7), evaluated with zero-padded 3D FFTs
+ * (eq. 10); its singular cell is integrated over a sphere of equal volume (Section 2.2). The solve
+ * is restarted GMRES (Section 2.2) inside the block Gauss-Seidel / block Jacobi sweeps of Algorithm 1
+ * (Section 2.3, eqs. 21, 23) with the adaptive sub-domain tolerance e/10; sub-domains are slabs
+ * along z (the tool axis). All compute runs in sm_103a CUDA kernels on the current device.
+ *
+ * Conventions
+ *   - Time dependence e^{-i omega t}; mu = mu0; displacement currents ignored (Section 2.1).
+ *   - Grid: nx*ny*nz cubic cells of edge h; cell (ix,iy,iz) has centre origin + (i + 1/2) h. Arrays
+ *     over cells are x-fastest: index (iz*ny + iy)*nx + ix.
+ *   - Complex arrays on the host are interleaved (re, im) doubles. Fields are component-major:
+ *     [3][nz][ny][nx] complex.
+ *   - sigma6: absolute conductivity per cell, [nz][ny][nx][6] doubles (xx, yy, zz, xy, xz, yz), S/m;
+ *     the symmetric tensor must be positive definite (Appendix C tensors are).
+ *   - A magnetic dipole of moment m (A m^2) is the magnetic current J^H = i omega mu0 m delta(r - r_s)
+ *     in eq. 1, so H0 is the textbook dipole field.
+ *   - Ownership: the caller owns every pointer it passes; the library copies inputs during the call
+ *     and writes outputs before returning. Device memory used internally belongs to the context.
+ *   - Errors: every call returns an ie_status; no exception crosses the ABI. ie_last_error() gives
+ *     the context's last message. A failed call leaves the context usable unless it returns
+ *     IE_ECUDA (a CUDA runtime error; the context should then be destroyed).
+ *   - Threads: one context per host thread. Work is issued on the context's stream (default: the
+ *     legacy default stream; see ie_set_stream) and every host-buffer call synchronises it.
+ */
+#ifndef IE_GB300_H
+#define IE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IE_OK = 0,
+  IE_EINVAL = 1,   /* invalid argument (sizes, NaN/indefinite sigma, source/receiver on a cell centre) */
+  IE_ENOMEM = 2,   /* device or host allocation failed */
+  IE_ECUDA = 3,    /* CUDA runtime error */
+  IE_ENOCONV = 4,  /* iteration limit reached; outputs hold the best iterate, info is filled */
+  IE_ESTATE = 5    /* call out of order (e.g. ie_solve before ie_set_contrast) */
+} ie_status;
+
+typedef enum { IE_DD_NONE = 0, IE_DD_JACOBI = 1, IE_DD_GAUSS_SEIDEL = 2 } ie_dd_mode;
+
+typedef enum {
+  IE_PREC_MIXED = 0, /* complex64 FFT convolution and Krylov vectors, FP64 outer residual/refinement */
+  IE_PREC_FP64 = 1   /* complex128 everywhere */
+} ie_precision;
+
+typedef struct {
+  int32_t nx, ny, nz;
+  double origin[3]; /* minimum corner of the grid, metres */
+} ie_grid;
+
+typedef struct {
+  double pos[3];    /* metres */
+  double moment[3]; /* A m^2 */
+} ie_dipole;
+
+typedef struct {
+  int32_t n_blocks;       /* number of sub-domains along z (>= 1); ignored for IE_DD_NONE */
+  const int32_t* z_split; /* n_blocks+1 increasing z indices from 0 to nz, or NULL for equal slabs */
+  int32_t restart;        /* GMRES restart length m (default 30) */
+  int32_t max_outer;      /* maximum DD sweeps / refinement steps (default 50) */
+  int32_t max_inner;      /* maximum GMRES iterations per block solve (default 20*restart) */
+  int32_t precision;      /* ie_precision (default IE_PREC_MIXED) */
+  int32_t adaptive;       /* 1: block tolerance e/10 (Algorithm 1, "-A"); 0: fixed_tol ("-F") */
+  double fixed_tol;       /* block tolerance when adaptive == 0 */
+} ie_opts;
+
+#define IE_MAX_HISTORY 128
+typedef struct {
+  int32_t outer_iters;       /* DD sweeps (or refinement steps) performed, summed over sources */
+  int32_t gmres_iters_total; /* Arnoldi steps over all block solves and sources */
+  int32_t matvecs;           /* block operator applications (Arnoldi + restart residuals) */
+  int32_t n_history;         /* entries used in residual_history (first source only) */
+  double final_rel_residual; /* max over sources of the FP64 whole-domain e (eq. 9) at exit */
+  double seconds;            /* wall time of the call */
+  double residual_history[IE_MAX_HISTORY]; /* e before the first sweep and after each sweep */
+  int32_t sweep_gmres_iters[IE_MAX_HISTORY]; /* GMRES iterations per sweep (first source) */
+} ie_info;
+
+typedef struct ie_ctx ie_ctx;
+
+/* Default options (restart 30, max_outer 50, max_inner 600, mixed precision, adaptive). */
+void ie_default_opts(ie_opts* opts);
+
+/* Create a context for one grid, cell size h (m), background sigma0 (S/m) and frequency (Hz)
+ * (Section 2.1: homogeneous isotropic background; eq. 7: k0 = sqrt(i omega mu0 sigma0)). Tabulates
+ * the Green kernel in FP64 (eq. 5 plus the equal-volume-sphere self term of Section 2.2), takes its
+ * FFT (eq. 10, padding to the next power of two >= 2n per axis, at most 1024) and stores one octant
+ * of the six symmetric components in complex128 and complex64. Requires 1 <= nx, ny, nz <= 512.
+ * Returns IE_EINVAL for bad sizes or non-positive h, sigma0, freq. *out is NULL on failure. */
+ie_status ie_create(const ie_grid* grid, double cell_size_m, double sigma0_S_per_m, double freq_hz, ie_ctx** out);
+
+/* Issue all work on this CUDA stream (a cudaStream_t passed as void*; NULL = legacy default). */
+ie_status ie_set_stream(ie_ctx* ctx, void* cuda_stream);
+
+/* Set the conductivity model from a host array sigma6 [nz][ny][nx][6] (see Conventions); forms the
+ * contrast dsigma = sigma - sigma0 I (Section 2.1). IE_EINVAL if any value is not finite or a tensor
+ * is not positive definite (the previous model is then kept only if the call fails before upload). */
+ie_status ie_set_contrast(ie_ctx* ctx, const double* sigma6);
+/* Same, from a device array with the same layout. */
+ie_status ie_set_contrast_dev(ie_ctx* ctx, const double* sigma6_dev);
+
+/* Forward model for n_src transmitters and n_rx receivers (Algorithm 1 and eq. 4).
+ *   dd_mode IE_DD_NONE: one GMRES on the whole grid (Section 2.2);
+ *           IE_DD_GAUSS_SEIDEL / IE_DD_JACOBI: Algorithm 1 with opts->n_blocks slabs along z.
+ *   tol: target whole-domain relative residual e (eq. 9), verified in FP64.
+ *   rx_xyz: [n_rx][3] receiver positions; H_out: [n_src][n_rx][3] complex (interleaved), total H.
+ *   opts and info may be NULL. Sources/receivers closer than 1e-9 h to a cell centre -> IE_EINVAL.
+ * Returns IE_ENOCONV (with H_out and info written for the best iterate) when max_outer sweeps or the
+ * inner iteration limits end before e <= tol. */
+ie_status ie_solve(ie_ctx* ctx, int32_t n_src, const ie_dipole* src, int32_t n_rx, const double* rx_xyz,
+                   int32_t dd_mode, double tol, const ie_opts* opts, double* H_out, ie_info* info);
+
+/* Copy the electric field of the last source of the last ie_solve to the host ([3][nz][ny][nx]
+ * complex, interleaved). IE_ESTATE if no solve has run. */
+ie_status ie_get_field(ie_ctx* ctx, double* E_out);
+
+/* Apply the operator of one sub-domain, y = (I - G^(ii) dsigma^(i)) x (eq. 8 restricted to the slab
+ * z in [z0, z0+nz), block-sized FFT convolution as used inside GMRES), on host arrays
+ * x, y: [3][nz][ny][nx] complex. precision selects the complex64 or complex128 kernels. */
+ie_status ie_matvec(ie_ctx* ctx, int32_t precision, int32_t z0, int32_t nz, const double* x, double* y);
+
+/* The same complex64 operator on device arrays (x_dev, y_dev: [3][nz][ny][nx] float2, distinct),
+ * enqueued on the context stream without synchronising. */
+ie_status ie_matvec_dev(ie_ctx* ctx, int32_t z0, int32_t nz, const void* x_dev, void* y_dev);
+
+/* Interaction field of eqs. 21/23: y = G^(ts) dsigma^(s) x for a source slab [zs0, zs0+nzs) and a
+ * target slab [zt0, zt0+nzt), computed with the whole-grid spectra (complex128 kernels). x: source
+ * field [3][nzs][ny][nx], y: target field [3][nzt][ny][nx], host, complex. */
+ie_status ie_interaction(ie_ctx* ctx, int32_t zs0, int32_t nzs, int32_t zt0, int32_t nzt, const double* x, double* y);
+
+/* Restarted GMRES (Section 2.2) on one sub-domain operator (slab [z0, z0+nz)): solves
+ * (I - G^(ii) dsigma^(i)) x = b from x0 (NULL = 0) to ||b - A x|| <= tol ||b||, host arrays.
+ * iters and rel_res (true final residual) may be NULL. IE_ENOCONV when max_iter is reached. */
+ie_status ie_gmres(ie_ctx* ctx, int32_t precision, int32_t z0, int32_t nz, const double* b, const double* x0,
+                   double tol, int32_t restart, int32_t max_iter, double* x, int32_t* iters, double* rel_res);
+
+/* Green spectra for a slab of nz_set cells (nz_set = a sub-domain's nz, or the grid nz for the
+ * interaction spectra): component comp (0 xx, 1 yy, 2 zz, 3 xy, 4 xz, 5 yz) of the octant
+ * F[K](kx, ky, kz) / (Lx Ly Lz) for 0 <= k <= L/2 per axis, complex128, layout [kz][ky][kx].
+ * dims_out (may be NULL) receives (Lx, Ly, Lz). */
+ie_status ie_green_spectrum(ie_ctx* ctx, int32_t nz_set, int32_t comp, double* out, int32_t* dims_out);
+
+/* Incident electric field E0 of one dipole on the cell centres, [3][nz][ny][nx] complex (host). */
+ie_status ie_incident_field(ie_ctx* ctx, const ie_dipole* src, double* E0_out);
+
+/* Total magnetic field at receivers for a given electric field E ([3][nz][ny][nx] complex, host):
+ * H = H0 + sum_j dv grad g(r - r_j) x (dsigma_j E_j) (eqs. 4, 6). H_out [n_rx][3] complex. */
+ie_status ie_receiver_fields(ie_ctx* ctx, const double* E, const ie_dipole* src, int32_t n_rx, const double* rx_xyz,
+                             double* H_out);
+
+/* Padded FFT lengths (Lx, Ly, Lz) the context uses for a slab of nz_set cells. */
+ie_status ie_fft_dims(const ie_ctx* ctx, int32_t nz_set, int32_t* dims_out);
+
+/* Last error message of the context (never NULL; "" when none). */
+const char* ie_last_error(const ie_ctx* ctx);
+
+/* Release the context and all its device memory. NULL is allowed. */
+void ie_destroy(ie_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IE_GB300_H */

@@ -1,0 +1,216 @@
+// Pass kernels of the zero-padded FFT convolution G (dsigma x) (eq. 10 of the paper).
+//
+// Layouts (complex = float2 or double2, x fastest):
+//   source field x, output y     [3][nz][ny][nx]      (component stride given per call)
+//   contrast dsigma              [6][Nz][ny][nx] real (xx, yy, zz, xy, xz, yz)
+//   A (after x-FFT)              [3][nz][ny][Lx]
+//   B (after y-FFT)              [3][nz][Ly][Lx]
+//   Green spectra (one octant)   [6][Lz/2+1][Ly/2+1][Lx/2+1], already scaled by 1/(Lx Ly Lz)
+// Pass order: P1 contrast + x-FFT, P2 y-FFT, P3 z-FFT + 3x3 spectral product + inverse z-FFT,
+// P4 inverse y-FFT, P5 inverse x-FFT + crop + epilogue. The zero padding is never stored: a pass
+// only loads the valid part of each pencil and only stores the part the next pass needs.
+#pragma once
+#include "conv.cuh"
+#include "fft.cuh"
+
+namespace ie {
+
+constexpr int kThreads = 256;
+
+template <typename T, int L> struct RowCfg {  // pencils contiguous in memory (x axis)
+  static constexpr int TT = Plan<T, L>::TT;
+  static constexpr int P0 = kThreads / TT;
+  static constexpr int P = P0 < 1 ? 1 : (P0 > 64 ? 64 : P0);  // pencils per block
+};
+template <typename T, int L> struct LaneCfg {  // pencils strided, W neighbouring pencils per block
+  static constexpr int TT = Plan<T, L>::TT;
+  static constexpr int W0 = kThreads / TT;
+  static constexpr int W = W0 < 1 ? 1 : (W0 > 32 ? 32 : W0);
+};
+
+// ---------------------------------------------------------------- P1: J = dsigma x, x-FFT
+template <typename T, int L>
+__global__ void __launch_bounds__(kThreads) k_p1_contrast_fftx(
+    const C<T>* __restrict__ x, long x_cs, const T* __restrict__ ds, long d_cs,
+    C<T>* __restrict__ A, long A_cs, int nx, long nrows, const C<T>* __restrict__ tw) {
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, P = RowCfg<T, L>::P;
+  __shared__ C<T> smem[P * RowSM<T>::words(L)];
+  const int t = threadIdx.x, p = threadIdx.y;
+  const long row = (long)blockIdx.x * P + p;
+  const bool act = row < nrows;
+  RowSM<T> sm{smem + p * RowSM<T>::words(L)};
+  C<T> J[3][E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int i = t + TT * m;
+    if (act && i < nx) {
+      const long o = row * nx + i;
+      const C<T> x0 = x[o], x1 = x[x_cs + o], x2 = x[2 * x_cs + o];
+      const T sxx = ds[o], syy = ds[d_cs + o], szz = ds[2 * d_cs + o];
+      const T sxy = ds[3 * d_cs + o], sxz = ds[4 * d_cs + o], syz = ds[5 * d_cs + o];
+      J[0][m] = mk<T>(sxx * x0.x + sxy * x1.x + sxz * x2.x, sxx * x0.y + sxy * x1.y + sxz * x2.y);
+      J[1][m] = mk<T>(sxy * x0.x + syy * x1.x + syz * x2.x, sxy * x0.y + syy * x1.y + syz * x2.y);
+      J[2][m] = mk<T>(sxz * x0.x + syz * x1.x + szz * x2.x, sxz * x0.y + syz * x1.y + szz * x2.y);
+    } else {
+      J[0][m] = J[1][m] = J[2][m] = czero<C<T>>();
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) pencil_fft<T, L, -1>(J[c], t, sm, tw);
+  if (act) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int m = 0; m < E; ++m) A[c * A_cs + row * L + t + TT * m] = J[c][m];
+  }
+}
+
+// ---------------------------------------------------------------- P5: inverse x-FFT, crop, epilogue
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(kThreads) k_p5_ifftx_epilogue(
+    const C<T>* __restrict__ A, long A_cs, int nx, long nrows,
+    const C<T>* __restrict__ xin, long x_cs, C<T>* __restrict__ y, long y_cs,
+    double2* __restrict__ r, long r_cs, const double2* __restrict__ b, long b_cs,
+    const C<T>* __restrict__ tw) {
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, P = RowCfg<T, L>::P;
+  __shared__ C<T> smem[P * RowSM<T>::words(L)];
+  const int t = threadIdx.x, p = threadIdx.y, c = blockIdx.y;
+  const long row = (long)blockIdx.x * P + p;
+  const bool act = row < nrows;
+  RowSM<T> sm{smem + p * RowSM<T>::words(L)};
+  C<T> v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = act ? A[c * A_cs + row * L + t + TT * m] : czero<C<T>>();
+  pencil_fft<T, L, +1>(v, t, sm, tw);
+  if (!act) return;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int i = t + TT * m;
+    if (i < nx) {
+      const long o = row * nx + i;
+      if constexpr (MODE == EPI_APPLY) {
+        y[c * y_cs + o] = xin[c * x_cs + o] - v[m];
+      } else if constexpr (MODE == EPI_CONV) {
+        y[c * y_cs + o] = v[m];
+      } else if constexpr (MODE == EPI_ACCUM128) {
+        r[c * r_cs + o] = r[c * r_cs + o] + to_c64(v[m]);
+      } else {  // EPI_RESID128: r = b - x + G(dsigma x)
+        r[c * r_cs + o] = b[c * b_cs + o] - to_c64(xin[c * x_cs + o]) + to_c64(v[m]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- strided FFT (P2, P4, setup)
+// Pencil element e of lane `lane`, batch z, component c sits at c*cs + z*zs + e*es + lane.
+template <typename T, int L, int SIGN>
+__global__ void __launch_bounds__(kThreads) k_lanes_fft(
+    const C<T>* __restrict__ in, long in_cs, long in_zs, long in_es, int n_in,
+    C<T>* __restrict__ out, long out_cs, long out_zs, long out_es, int n_out, int nlanes,
+    const C<T>* __restrict__ tw) {
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = LaneCfg<T, L>::W;
+  __shared__ C<T> smem[L * W];
+  const int w = threadIdx.x, t = threadIdx.y;
+  const long z = blockIdx.y, c = blockIdx.z;
+  const int lane = blockIdx.x * W + w;
+  const bool act = lane < nlanes;
+  LaneSM<T, W> sm{smem + w};
+  const C<T>* src = in + c * in_cs + z * in_zs + lane;
+  C<T> v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int e = t + TT * m;
+    v[m] = (act && e < n_in) ? src[(long)e * in_es] : czero<C<T>>();
+  }
+  pencil_fft<T, L, SIGN>(v, t, sm, tw);
+  if (!act) return;
+  C<T>* dst = out + c * out_cs + z * out_zs + lane;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int e = t + TT * m;
+    if (e < n_out) dst[(long)e * out_es] = v[m];
+  }
+}
+
+// ---------------------------------------------------------------- P3: z-FFT, Green product, inverse
+// B holds planes of Ly*Lx; the source occupies pencil positions [os, os + nzs), the target is read
+// back from [ot, ot + nzt). With os = ot = 0 this is a block's own convolution; with the whole-domain
+// spectra and os/ot the blocks' z offsets it is the interaction between two sub-domains.
+template <typename T, int L>
+__global__ void __launch_bounds__(kThreads) k_p3_spectral(
+    const C<T>* __restrict__ Bin, long in_cs, int nzs, int os, C<T>* __restrict__ Bout, long out_cs,
+    int nzt, int ot, const C<T>* __restrict__ G, int Lx, int Ly, const C<T>* __restrict__ tw) {
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = LaneCfg<T, L>::W;
+  __shared__ C<T> smem[L * W];
+  const int w = threadIdx.x, t = threadIdx.y;
+  const int kx = blockIdx.x * W + w, ky = blockIdx.y;
+  const bool act = kx < Lx;
+  LaneSM<T, W> sm{smem + w};
+  const long plane = (long)Ly * Lx, off = (long)ky * Lx + kx;
+  C<T> v[3][E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int z = t + TT * m - os;
+    const bool ok = act && z >= 0 && z < nzs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c][m] = ok ? Bin[c * in_cs + z * plane + off] : czero<C<T>>();
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) pencil_fft<T, L, -1>(v[c], t, sm, tw);
+  {
+    const int ox = Lx / 2 + 1, oy = Ly / 2 + 1, oz = L / 2 + 1;
+    const long ocs = (long)oz * oy * ox;
+    const bool xlo = kx <= Lx / 2, ylo = ky <= Ly / 2;
+    const int ix = xlo ? kx : Lx - kx, iy = ylo ? ky : Ly - ky;
+    const T sxy = (xlo == ylo) ? (T)1 : (T)-1;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int kz = t + TT * m;
+      const bool zlo = kz <= L / 2;
+      const int iz = zlo ? kz : L - kz;
+      const T sxz = (xlo == zlo) ? (T)1 : (T)-1, syz = (ylo == zlo) ? (T)1 : (T)-1;
+      if (act) {
+        const C<T>* g = G + ((long)iz * oy + iy) * ox + ix;
+        const C<T> gxx = __ldg(g), gyy = __ldg(g + ocs), gzz = __ldg(g + 2 * ocs);
+        const C<T> gxy = sxy * __ldg(g + 3 * ocs), gxz = sxz * __ldg(g + 4 * ocs), gyz = syz * __ldg(g + 5 * ocs);
+        const C<T> j0 = v[0][m], j1 = v[1][m], j2 = v[2][m];
+        v[0][m] = cmul(gxx, j0) + cmul(gxy, j1) + cmul(gxz, j2);
+        v[1][m] = cmul(gxy, j0) + cmul(gyy, j1) + cmul(gyz, j2);
+        v[2][m] = cmul(gxz, j0) + cmul(gyz, j1) + cmul(gzz, j2);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) pencil_fft<T, L, +1>(v[c], t, sm, tw);
+  if (!act) return;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int z = t + TT * m - ot;
+    if (z >= 0 && z < nzt) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Bout[c * out_cs + z * plane + off] = v[c][m];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- contiguous full FFT (setup)
+template <typename T, int L, int SIGN>
+__global__ void __launch_bounds__(kThreads) k_rows_fft(C<T>* __restrict__ data, long nrows,
+                                                      const C<T>* __restrict__ tw) {
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, P = RowCfg<T, L>::P;
+  __shared__ C<T> smem[P * RowSM<T>::words(L)];
+  const int t = threadIdx.x, p = threadIdx.y;
+  const long row = (long)blockIdx.x * P + p;
+  const bool act = row < nrows;
+  RowSM<T> sm{smem + p * RowSM<T>::words(L)};
+  C<T> v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = act ? data[row * L + t + TT * m] : czero<C<T>>();
+  pencil_fft<T, L, SIGN>(v, t, sm, tw);
+  if (act) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) data[row * L + t + TT * m] = v[m];
+  }
+}
+
+}  // namespace ie

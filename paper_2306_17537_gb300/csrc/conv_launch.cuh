@@ -1,0 +1,151 @@
+// Host-side launchers for the convolution passes: map a runtime pencil length to the kernel
+// template instantiated for it. Explicitly instantiated for float and double in conv_f32.cu and
+// conv_f64.cu so the two precisions compile in parallel.
+#pragma once
+#include "conv.cuh"
+#include "conv_kernels.cuh"
+
+namespace ie {
+
+#define IE_FOR_EACH_L(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+
+inline bool supported_pencil_impl(int L) {
+  switch (L) {
+#define IE_CASE(N) case N:
+    IE_FOR_EACH_L(IE_CASE)
+#undef IE_CASE
+    return true;
+    default:
+      return false;
+  }
+}
+
+
+template <typename T>
+cudaError_t ConvLaunch<T>::p1(int L, const C<T>* x, long x_cs, const T* ds, long d_cs, C<T>* A, long A_cs, int nx,
+                              long nrows, const C<T>* tw, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  switch (L) {
+#define IE_CASE(N)                                                                              \
+  case N: {                                                                                     \
+    constexpr int P = RowCfg<T, N>::P;                                                          \
+    dim3 blk(Plan<T, N>::TT, P), grd((unsigned)((nrows + P - 1) / P));                         \
+    k_p1_contrast_fftx<T, N><<<grd, blk, 0, s>>>(x, x_cs, ds, d_cs, A, A_cs, nx, nrows, tw);    \
+    break;                                                                                      \
+  }
+    IE_FOR_EACH_L(IE_CASE)
+#undef IE_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ConvLaunch<T>::p5(int L, int mode, const C<T>* A, long A_cs, int nx, long nrows, const C<T>* xin,
+                              long x_cs, C<T>* y, long y_cs, double2* r, long r_cs, const double2* b, long b_cs,
+                              const C<T>* tw, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  switch (L) {
+#define IE_CASE(N)                                                                                               \
+  case N: {                                                                                                      \
+    constexpr int P = RowCfg<T, N>::P;                                                                           \
+    dim3 blk(Plan<T, N>::TT, P), grd((unsigned)((nrows + P - 1) / P), 3);                                       \
+    switch (mode) {                                                                                              \
+      case EPI_APPLY:                                                                                            \
+        k_p5_ifftx_epilogue<T, N, EPI_APPLY><<<grd, blk, 0, s>>>(A, A_cs, nx, nrows, xin, x_cs, y, y_cs, r,     \
+                                                                 r_cs, b, b_cs, tw);                             \
+        break;                                                                                                   \
+      case EPI_CONV:                                                                                             \
+        k_p5_ifftx_epilogue<T, N, EPI_CONV><<<grd, blk, 0, s>>>(A, A_cs, nx, nrows, xin, x_cs, y, y_cs, r,      \
+                                                                r_cs, b, b_cs, tw);                              \
+        break;                                                                                                   \
+      case EPI_ACCUM128:                                                                                         \
+        k_p5_ifftx_epilogue<T, N, EPI_ACCUM128><<<grd, blk, 0, s>>>(A, A_cs, nx, nrows, xin, x_cs, y, y_cs, r,  \
+                                                                    r_cs, b, b_cs, tw);                          \
+        break;                                                                                                   \
+      case EPI_RESID128:                                                                                         \
+        k_p5_ifftx_epilogue<T, N, EPI_RESID128><<<grd, blk, 0, s>>>(A, A_cs, nx, nrows, xin, x_cs, y, y_cs, r,  \
+                                                                    r_cs, b, b_cs, tw);                          \
+        break;                                                                                                   \
+      default:                                                                                                   \
+        return cudaErrorInvalidValue;                                                                            \
+    }                                                                                                            \
+    break;                                                                                                       \
+  }
+    IE_FOR_EACH_L(IE_CASE)
+#undef IE_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ConvLaunch<T>::lanes(int L, int sign, const C<T>* in, long in_cs, long in_zs, long in_es, int n_in,
+                                 C<T>* out, long out_cs, long out_zs, long out_es, int n_out, int nlanes, int nbatch,
+                                 int ncomp, const C<T>* tw, cudaStream_t s) {
+  if (nbatch <= 0 || nlanes <= 0 || ncomp <= 0) return cudaSuccess;
+  switch (L) {
+#define IE_CASE(N)                                                                                               \
+  case N: {                                                                                                      \
+    constexpr int W = LaneCfg<T, N>::W;                                                                          \
+    dim3 blk(W, Plan<T, N>::TT), grd((unsigned)((nlanes + W - 1) / W), (unsigned)nbatch, (unsigned)ncomp);      \
+    if (sign < 0)                                                                                                \
+      k_lanes_fft<T, N, -1><<<grd, blk, 0, s>>>(in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es,      \
+                                                 n_out, nlanes, tw);                                             \
+    else                                                                                                         \
+      k_lanes_fft<T, N, 1><<<grd, blk, 0, s>>>(in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es,       \
+                                                n_out, nlanes, tw);                                              \
+    break;                                                                                                       \
+  }
+    IE_FOR_EACH_L(IE_CASE)
+#undef IE_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ConvLaunch<T>::p3(int L, const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt,
+                              int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, cudaStream_t s) {
+  switch (L) {
+#define IE_CASE(N)                                                                                            \
+  case N: {                                                                                                   \
+    constexpr int W = LaneCfg<T, N>::W;                                                                       \
+    dim3 blk(W, Plan<T, N>::TT), grd((unsigned)((Lx + W - 1) / W), (unsigned)Ly);                            \
+    k_p3_spectral<T, N><<<grd, blk, 0, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw);       \
+    break;                                                                                                    \
+  }
+    IE_FOR_EACH_L(IE_CASE)
+#undef IE_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ConvLaunch<T>::rows(int L, int sign, C<T>* data, long nrows, const C<T>* tw, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  switch (L) {
+#define IE_CASE(N)                                                                    \
+  case N: {                                                                           \
+    constexpr int P = RowCfg<T, N>::P;                                                \
+    dim3 blk(Plan<T, N>::TT, P), grd((unsigned)((nrows + P - 1) / P));               \
+    if (sign < 0)                                                                     \
+      k_rows_fft<T, N, -1><<<grd, blk, 0, s>>>(data, nrows, tw);                      \
+    else                                                                              \
+      k_rows_fft<T, N, 1><<<grd, blk, 0, s>>>(data, nrows, tw);                       \
+    break;                                                                            \
+  }
+    IE_FOR_EACH_L(IE_CASE)
+#undef IE_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ie

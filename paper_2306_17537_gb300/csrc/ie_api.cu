@@ -1,0 +1,901 @@
+// C-ABI entry points and host orchestration of the IE forward model (include/ie.h).
+//
+// Solve structure (Algorithm 1 of the paper with FP64 iterative refinement):
+//   E := E0;  R := E0 - (I - G dsigma) E in FP64 on the whole grid;  e := |R| / |E0|     (eq. 9)
+//   while e > tol:
+//     for each sub-domain i (Gauss-Seidel order, or all from the same R for Jacobi):
+//       b_i = R_i + A_ii E_i is the block right-hand side of eqs. 21/23, so GMRES(A_ii, b_i,
+//       x0 = E_i, tol_i) is run in correction form: delta = GMRES(A_ii, R_i, x0 = 0,
+//       tol_i |b_i| / |R_i|), E_i += delta (identical Krylov iterates);
+//       Gauss-Seidel: R_j += G^(ji) dsigma_i delta for the later blocks j > i (interaction update)
+//     R := E0 - (I - G dsigma) E in FP64; e := |R| / |E0|
+// With IE_PREC_MIXED the block GMRES runs on complex64 vectors with complex64 FFT convolutions and
+// the FP64 residual carries the accuracy; with IE_PREC_FP64 everything is complex128.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "conv.cuh"
+#include "green.cuh"
+#include "ie.h"
+
+namespace ie {
+
+static const double kMu0 = 4.0e-7 * M_PI;
+
+static int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t b) {
+    if (b <= bytes && p) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = b;
+    return cudaSuccess;
+  }
+  template <typename X> X* as() const { return reinterpret_cast<X*>(p); }
+};
+
+struct SpecSet {
+  int nz_set = 0, Lz = 0;
+  DevBuf G64, G32;  // octants, 6 components
+};
+
+}  // namespace ie
+
+using namespace ie;
+
+struct ie_ctx {
+  int nx = 0, ny = 0, nz = 0;
+  long N = 0;
+  double origin[3] = {0, 0, 0};
+  double h = 0, sigma0 = 0, freq = 0, omega = 0;
+  double2 k0{}, self{};
+  int Lx = 0, Ly = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  DevBuf tw64, tw32;
+  DevBuf ds64, ds32, s6_stage;
+  bool has_contrast = false;
+  std::vector<SpecSet*> specs;
+
+  DevBuf A32, B32, A64, B64;  // convolution workspaces
+  long zcap32 = 0, zcap64 = 0;
+
+  DevBuf E, E0, R;  // c128 whole-grid fields
+  bool has_field = false;
+
+  // Krylov workspace (one precision at a time; sized on demand)
+  DevBuf V, kx, kb, kt1, kt2;
+  DevBuf part, dh, dh2, dnrm, dy, flag, rxdev, Hdev, rxpart;
+  double2* hpin = nullptr;  // pinned host scratch for small reductions
+
+  ~ie_ctx() {
+    for (auto* s : specs) delete s;
+    if (hpin) cudaFreeHost(hpin);
+  }
+};
+
+namespace {
+
+ie_status fail(ie_ctx* c, ie_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+#define CK(expr)                                                                              \
+  do {                                                                                        \
+    cudaError_t _e = (expr);                                                                  \
+    if (_e != cudaSuccess)                                                                    \
+      return fail(c, _e == cudaErrorMemoryAllocation ? IE_ENOMEM : IE_ECUDA,                  \
+                  std::string(#expr) + ": " + cudaGetErrorString(_e));                        \
+  } while (0)
+
+#define CKS(expr)                 \
+  do {                            \
+    ie_status _s = (expr);        \
+    if (_s != IE_OK) return _s;   \
+  } while (0)
+
+template <typename T> const C<T>* twid(const ie_ctx* c);
+template <> const float2* twid<float>(const ie_ctx* c) { return c->tw32.as<float2>(); }
+template <> const double2* twid<double>(const ie_ctx* c) { return c->tw64.as<double2>(); }
+template <typename T> const T* dsig(const ie_ctx* c);
+template <> const float* dsig<float>(const ie_ctx* c) { return c->ds32.as<float>(); }
+template <> const double* dsig<double>(const ie_ctx* c) { return c->ds64.as<double>(); }
+template <typename T> const C<T>* spec(const SpecSet* s);
+template <> const float2* spec<float>(const SpecSet* s) { return s->G32.as<float2>(); }
+template <> const double2* spec<double>(const SpecSet* s) { return s->G64.as<double2>(); }
+
+// Green spectra for a slab of nz_set cells: FP64 tabulation -> FP64 3D FFT -> scaled octants.
+ie_status get_spec(ie_ctx* c, int nz_set, SpecSet** out) {
+  for (auto* s : c->specs)
+    if (s->nz_set == nz_set) {
+      *out = s;
+      return IE_OK;
+    }
+  const int Lz = next_pow2(2 * nz_set);
+  if (!supported_pencil(Lz)) return fail(c, IE_EINVAL, "padded z length above 1024");
+  auto* S = new SpecSet();
+  S->nz_set = nz_set;
+  S->Lz = Lz;
+  const long ox = c->Lx / 2 + 1, oy = c->Ly / 2 + 1, oz = Lz / 2 + 1, ocs = ox * oy * oz;
+  cudaError_t e1 = S->G64.ensure(sizeof(double2) * 6 * ocs);
+  cudaError_t e2 = e1 == cudaSuccess ? S->G32.ensure(sizeof(float2) * 6 * ocs) : e1;
+  DevBuf full;
+  cudaError_t e3 = e2 == cudaSuccess ? full.ensure(sizeof(double2) * (size_t)Lz * c->Ly * c->Lx) : e2;
+  if (e3 != cudaSuccess) {
+    delete S;
+    return fail(c, IE_ENOMEM, "allocating Green spectra");
+  }
+  const double scale = 1.0 / ((double)c->Lx * c->Ly * Lz);
+  double2* F = full.as<double2>();
+  const double2* tw = c->tw64.as<double2>();
+  for (int comp = 0; comp < 6; ++comp) {
+    cudaError_t e = launch_green_tab(F, comp, c->Lx, c->Ly, Lz, c->nx, c->ny, nz_set, c->h, c->k0, c->sigma0, c->self,
+                                     c->stream);
+    if (e == cudaSuccess) e = ConvLaunch<double>::rows(c->Lx, -1, F, (long)Lz * c->Ly, tw, c->stream);
+    if (e == cudaSuccess)  // y: element e of lane x in plane z at z*Ly*Lx + e*Lx + x
+      e = ConvLaunch<double>::lanes(c->Ly, -1, F, 0, (long)c->Ly * c->Lx, c->Lx, c->Ly, F, 0, (long)c->Ly * c->Lx,
+                                    c->Lx, c->Ly, c->Lx, Lz, 1, tw, c->stream);
+    if (e == cudaSuccess)  // z: element e of lane x in row y at y*Lx + e*Ly*Lx + x
+      e = ConvLaunch<double>::lanes(Lz, -1, F, 0, c->Lx, (long)c->Ly * c->Lx, Lz, F, 0, c->Lx, (long)c->Ly * c->Lx, Lz,
+                                    c->Lx, c->Ly, 1, tw, c->stream);
+    if (e == cudaSuccess)
+      e = launch_extract_octant(F, c->Lx, c->Ly, Lz, scale, S->G64.as<double2>() + comp * ocs,
+                                S->G32.as<float2>() + comp * ocs, c->stream);
+    if (e != cudaSuccess) {
+      delete S;
+      return fail(c, IE_ECUDA, std::string("Green spectra: ") + cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);  // `full` is freed on return
+  if (e != cudaSuccess) {
+    delete S;
+    return fail(c, IE_ECUDA, std::string("Green spectra: ") + cudaGetErrorString(e));
+  }
+  c->specs.push_back(S);
+  *out = S;
+  return IE_OK;
+}
+
+template <typename T> ie_status ensure_conv_ws(ie_ctx* c, int zcap) {
+  long& cap = std::is_same<T, float>::value ? c->zcap32 : c->zcap64;
+  DevBuf& A = std::is_same<T, float>::value ? c->A32 : c->A64;
+  DevBuf& B = std::is_same<T, float>::value ? c->B32 : c->B64;
+  if (zcap <= cap) return IE_OK;
+  CK(A.ensure(sizeof(C<T>) * 3 * (size_t)zcap * c->ny * c->Lx));
+  CK(B.ensure(sizeof(C<T>) * 3 * (size_t)zcap * c->Ly * c->Lx));
+  cap = zcap;
+  return IE_OK;
+}
+
+// One FFT convolution G^(ts) dsigma^(s) x with the given spectra and epilogue (see conv_kernels.cuh).
+//   x: source field, components at stride x_cs, covering the slab [zs0, zs0 + nzs) of the grid;
+//   os/ot: pencil positions of the source / target slab inside the padded z axis of `S`.
+template <typename T>
+ie_status conv(ie_ctx* c, const SpecSet* S, const C<T>* x, long x_cs, int zs0, int nzs, int os, int nzt, int ot,
+               int mode, const C<T>* xin, long xin_cs, C<T>* y, long y_cs, double2* r, long r_cs, const double2* b,
+               long b_cs) {
+  CKS(ensure_conv_ws<T>(c, std::max(nzs, nzt)));
+  const long zc = std::is_same<T, float>::value ? c->zcap32 : c->zcap64;
+  C<T>* A = (std::is_same<T, float>::value ? c->A32 : c->A64).template as<C<T>>();
+  C<T>* B = (std::is_same<T, float>::value ? c->B32 : c->B64).template as<C<T>>();
+  const long A_cs = zc * c->ny * c->Lx, B_cs = zc * c->Ly * c->Lx;
+  const long nxy = (long)c->nx * c->ny;
+  const C<T>* tw = twid<T>(c);
+  cudaStream_t s = c->stream;
+  CK(ConvLaunch<T>::p1(c->Lx, x, x_cs, dsig<T>(c) + (long)zs0 * nxy, c->N, A, A_cs, c->nx, (long)nzs * c->ny, tw, s));
+  CK(ConvLaunch<T>::lanes(c->Ly, -1, A, A_cs, (long)c->ny * c->Lx, c->Lx, c->ny, B, B_cs, (long)c->Ly * c->Lx, c->Lx,
+                          c->Ly, c->Lx, nzs, 3, tw, s));
+  CK(ConvLaunch<T>::p3(S->Lz, B, B_cs, nzs, os, B, B_cs, nzt, ot, spec<T>(S), c->Lx, c->Ly, tw, s));
+  CK(ConvLaunch<T>::lanes(c->Ly, +1, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx, c->Lx,
+                          c->ny, c->Lx, nzt, 3, tw, s));
+  CK(ConvLaunch<T>::p5(c->Lx, mode, A, A_cs, c->nx, (long)nzt * c->ny, xin, xin_cs, y, y_cs, r, r_cs, b, b_cs, tw, s));
+  return IE_OK;
+}
+
+// Operator of one sub-domain, y = (I - G^(ii) dsigma^(i)) x, on block-local vectors.
+template <typename T> struct BlockOp {
+  ie_ctx* c;
+  int z0, nz;
+  const SpecSet* S;
+  long nb() const { return (long)nz * c->ny * c->nx; }
+  ie_status apply(const C<T>* x, C<T>* y) const {
+    return conv<T>(c, S, x, nb(), z0, nz, 0, nz, 0, EPI_APPLY, x, nb(), y, nb(), nullptr, 0, nullptr, 0);
+  }
+};
+
+template <typename T> ie_status make_block(ie_ctx* c, int z0, int nz, BlockOp<T>* op) {
+  if (z0 < 0 || nz < 1 || z0 + nz > c->nz) return fail(c, IE_EINVAL, "slab outside the grid");
+  if (!c->has_contrast) return fail(c, IE_ESTATE, "no contrast set");
+  SpecSet* S = nullptr;
+  CKS(get_spec(c, nz, &S));
+  *op = BlockOp<T>{c, z0, nz, S};
+  return IE_OK;
+}
+
+ie_status ensure_scalars(ie_ctx* c) {
+  CK(c->part.ensure(sizeof(double2) * kRedBlocks * 160));
+  CK(c->dh.ensure(sizeof(double2) * 160));
+  CK(c->dh2.ensure(sizeof(double2) * 160));
+  CK(c->dnrm.ensure(sizeof(double2) * 8));
+  CK(c->dy.ensure(sizeof(double2) * 160));
+  CK(c->flag.ensure(sizeof(int) * 4));
+  if (!c->hpin) CK(cudaMallocHost(&c->hpin, sizeof(double2) * 320));
+  return IE_OK;
+}
+
+// FP64 sum of partials -> host
+ie_status reduce_to_host(ie_ctx* c, const double2* part, int nblk, int nk, double2* host) {
+  CK(launch_reduce(part, nblk, nk, c->dh2.as<double2>(), nullptr, nullptr, c->stream));
+  CK(cudaMemcpyAsync(c->hpin, c->dh2.as<double2>(), sizeof(double2) * nk, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::memcpy(host, c->hpin, sizeof(double2) * nk);
+  return IE_OK;
+}
+
+template <typename T> ie_status vnorm(ie_ctx* c, const C<T>* v, long n, double* out) {
+  CK(Krylov<T>::norm2(v, n, c->part.as<double2>(), c->stream));
+  double2 h;
+  CKS(reduce_to_host(c, c->part.as<double2>(), krylov_blocks(n), 1, &h));
+  *out = std::sqrt(std::max(h.x, 0.0));
+  return IE_OK;
+}
+
+ie_status norm_c128(ie_ctx* c, const double2* a, long a_cs, const float2* b, long b_cs, long n, double* out) {
+  CK(launch_norm2_c128(a, a_cs, b, b_cs, n, c->part.as<double2>(), c->stream));
+  double2 h;
+  CKS(reduce_to_host(c, c->part.as<double2>(), kRedBlocks, 1, &h));
+  *out = std::sqrt(std::max(h.x, 0.0));
+  return IE_OK;
+}
+
+struct GmresOut {
+  int iters = 0, matvecs = 0;
+  double rel = 0;
+  bool converged = false;
+};
+
+// Restarted GMRES(m) for A x = b (Saad & Schultz). Arnoldi: classical Gram-Schmidt with a second
+// pass when the projected norm drops below 1/sqrt(2) of the original (Daniel-Gragg-Kaufman-Stewart
+// test, decided on the device); FP64 Hessenberg and Givens rotations on the host; stopping on the
+// relative residual |b - A x| / |b| (eq. 9), confirmed by the true residual at every restart.
+// x holds x0 on entry unless x0_zero. Workspace c->V holds m+1 basis vectors.
+template <typename T>
+ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_zero, double tol, int m, int max_it,
+                GmresOut* out) {
+  const long n = 3 * A.nb();
+  cudaStream_t s = c->stream;
+  CKS(ensure_scalars(c));
+  if (m < 1 || m > 127) return fail(c, IE_EINVAL, "restart must be in [1, 127]");
+  CK(c->V.ensure(sizeof(C<T>) * (size_t)(m + 1) * n));
+  CK(c->kt1.ensure(sizeof(C<T>) * (size_t)n));
+  C<T>* V = c->V.as<C<T>>();
+  C<T>* tmp = c->kt1.as<C<T>>();
+  double2* part = c->part.as<double2>();
+  double2* dh = c->dh.as<double2>();
+  double2* dh2 = c->dh2.as<double2>();
+  double2* dn = c->dnrm.as<double2>();
+  int* flag = c->flag.as<int>();
+  *out = GmresOut();
+
+  double bnorm;
+  CKS(vnorm<T>(c, b, n, &bnorm));
+  if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(x, 0, sizeof(C<T>) * n, s));
+    out->converged = true;
+    return IE_OK;
+  }
+  double beta;
+  if (x0_zero) {
+    CK(cudaMemsetAsync(x, 0, sizeof(C<T>) * n, s));
+    CK(Krylov<T>::scale(b, V, n, nullptr, 1.0 / bnorm, s));
+    beta = bnorm;
+  } else {
+    CKS(A.apply(x, tmp));
+    out->matvecs++;
+    CK(Krylov<T>::rsub(b, tmp, n, part, s));
+    double2 h;
+    CKS(reduce_to_host(c, part, krylov_blocks(n), 1, &h));
+    beta = std::sqrt(std::max(h.x, 0.0));
+    if (beta / bnorm <= tol) {
+      out->rel = beta / bnorm;
+      out->converged = true;
+      return IE_OK;
+    }
+    CK(Krylov<T>::scale(tmp, V, n, nullptr, 1.0 / beta, s));
+  }
+  out->rel = beta / bnorm;
+  const int nblk = krylov_blocks(n);
+  std::vector<std::complex<double>> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  auto Hij = [&](int i, int j) -> std::complex<double>& { return H[(size_t)i * m + j]; };
+  while (true) {
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jd = 0;
+    bool breakdown = false;
+    for (int j = 0; j < m; ++j) {
+      C<T>* w = V + (size_t)(j + 1) * n;
+      CKS(A.apply(V + (size_t)j * n, w));
+      out->matvecs++;
+      const int nv = j + 1;
+      CK(Krylov<T>::dots(V, n, nv, w, n, part, true, nullptr, s));
+      CK(launch_reduce(part, nblk, nv + 1, dh, nullptr, nullptr, s));  // dh[0..j] = V^H w, dh[nv] = |w|^2
+      CK(Krylov<T>::update(V, n, nv, dh, w, n, part, nullptr, s));
+      CK(launch_reduce(part + (size_t)nv * kRedBlocks, nblk, 1, dn, nullptr, nullptr, s));
+      CK(launch_reorth_flag(dh + nv, dn, 0.5, flag, s));
+      CK(Krylov<T>::dots(V, n, nv, w, n, part, false, flag, s));
+      CK(launch_reduce(part, nblk, nv, dh2, dh, flag, s));  // dh += second-pass coefficients
+      CK(Krylov<T>::update(V, n, nv, dh2, w, n, part, flag, s));
+      CK(launch_reduce(part + (size_t)nv * kRedBlocks, nblk, 1, dn, nullptr, flag, s));
+      CK(Krylov<T>::scale(w, w, n, reinterpret_cast<const double*>(dn), 0.0, s));
+      CK(cudaMemcpyAsync(c->hpin, dh, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(c->hpin + nv, dn, sizeof(double2), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int i = 0; i < nv; ++i) Hij(i, j) = std::complex<double>(c->hpin[i].x, c->hpin[i].y);
+      const double hn = std::sqrt(std::max(c->hpin[nv].x, 0.0));
+      Hij(j + 1, j) = hn;
+      for (int i = 0; i < j; ++i) {
+        const std::complex<double> t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -std::conj(sn[i]) * Hij(i, j) + std::conj(cs[i]) * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const std::complex<double> a = Hij(j, j), d = Hij(j + 1, j);
+      const double den = std::sqrt(std::norm(a) + std::norm(d));
+      cs[j] = den != 0.0 ? std::conj(a) / den : 1.0;
+      sn[j] = den != 0.0 ? std::conj(d) / den : 0.0;
+      Hij(j, j) = cs[j] * a + sn[j] * d;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -std::conj(sn[j]) * g[j];
+      g[j] = cs[j] * g[j];
+      out->iters++;
+      jd = j + 1;
+      breakdown = (hn == 0.0);
+      const double est = std::abs(g[j + 1]) / bnorm;
+      if (!std::isfinite(est)) return fail(c, IE_ECUDA, "GMRES produced a non-finite residual");
+      if (est <= tol || breakdown || out->iters >= max_it) break;
+    }
+    for (int i = jd - 1; i >= 0; --i) {  // back substitution
+      std::complex<double> acc = g[i];
+      for (int k = i + 1; k < jd; ++k) acc -= Hij(i, k) * y[k];
+      y[i] = acc / Hij(i, i);
+    }
+    for (int i = 0; i < jd; ++i) c->hpin[i] = make_double2(y[i].real(), y[i].imag());
+    CK(cudaMemcpyAsync(c->dy.as<double2>(), c->hpin, sizeof(double2) * jd, cudaMemcpyHostToDevice, s));
+    CK(Krylov<T>::combine(V, n, jd, c->dy.as<double2>(), x, n, s));
+    CKS(A.apply(x, tmp));
+    out->matvecs++;
+    CK(Krylov<T>::rsub(b, tmp, n, part, s));
+    double2 h;
+    CKS(reduce_to_host(c, part, nblk, 1, &h));
+    beta = std::sqrt(std::max(h.x, 0.0));
+    out->rel = beta / bnorm;
+    if (out->rel <= tol) {
+      out->converged = true;
+      return IE_OK;
+    }
+    if (out->iters >= max_it || beta == 0.0) return IE_OK;
+    CK(Krylov<T>::scale(tmp, V, n, nullptr, 1.0 / beta, s));
+  }
+}
+
+ie_status check_point(ie_ctx* c, const double* p) {
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(p[a])) return fail(c, IE_EINVAL, "non-finite position");
+  double d2 = 0.0;
+  const int n[3] = {c->nx, c->ny, c->nz};
+  bool inside = true;
+  for (int a = 0; a < 3; ++a) {
+    const double u = (p[a] - c->origin[a]) / c->h - 0.5;  // fractional cell index of the nearest centre
+    const double k = std::round(u);
+    if (k < 0 || k > n[a] - 1) inside = false;
+    d2 += (u - k) * (u - k);
+  }
+  if (inside && std::sqrt(d2) < 1e-9) return fail(c, IE_EINVAL, "source or receiver on a cell centre");
+  return IE_OK;
+}
+
+// FP64 whole-grid residual R = E0 - (I - G dsigma) E and its relative norm e (eq. 9).
+ie_status full_residual(ie_ctx* c, double e0norm, double* e) {
+  SpecSet* S = nullptr;
+  CKS(get_spec(c, c->nz, &S));
+  const double2* Ed = c->E.as<double2>();
+  CKS(conv<double>(c, S, Ed, c->N, 0, c->nz, 0, c->nz, 0, EPI_RESID128, Ed, c->N, nullptr, 0, c->R.as<double2>(), c->N,
+                   c->E0.as<double2>(), c->N));
+  double rn;
+  CKS(norm_c128(c, c->R.as<double2>(), c->N, nullptr, 0, c->N, &rn));
+  *e = rn / e0norm;
+  if (!std::isfinite(*e)) return fail(c, IE_ECUDA, "non-finite residual");
+  return IE_OK;
+}
+
+struct SolveCfg {
+  int dd_mode;
+  std::vector<int> split;
+  int restart, max_outer, max_inner, precision, adaptive;
+  double fixed_tol, tol;
+};
+
+// Algorithm 1 (with FP64 refinement) for the source whose E0 is in c->E0; leaves E in c->E.
+template <typename T>
+ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) {
+  cudaStream_t s = c->stream;
+  const long nxy = (long)c->nx * c->ny;
+  const int M = (int)cfg.split.size() - 1;
+  CK(cudaMemcpyAsync(c->E.p, c->E0.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToDevice, s));
+  double e0norm;
+  CKS(norm_c128(c, c->E0.as<double2>(), c->N, nullptr, 0, c->N, &e0norm));
+  if (e0norm == 0.0) return IE_OK;  // no incident field inside the grid: E = 0
+  double e;
+  CKS(full_residual(c, e0norm, &e));
+  if (record) {
+    info->n_history = 1;
+    info->residual_history[0] = e;
+  }
+  std::vector<BlockOp<T>> ops(M);
+  long nbmax = 0;
+  for (int i = 0; i < M; ++i) {
+    CKS(make_block<T>(c, cfg.split[i], cfg.split[i + 1] - cfg.split[i], &ops[i]));
+    nbmax = std::max(nbmax, ops[i].nb());
+  }
+  SpecSet* Sfull = nullptr;
+  if (cfg.dd_mode == IE_DD_GAUSS_SEIDEL && M > 1) CKS(get_spec(c, c->nz, &Sfull));
+  CK(c->kb.ensure(sizeof(C<T>) * 3 * nbmax));
+  CK(c->kx.ensure(sizeof(C<T>) * 3 * nbmax));
+  CK(c->kt2.ensure(sizeof(C<T>) * 3 * nbmax));
+  C<T>* rhs = c->kb.as<C<T>>();
+  C<T>* dx = c->kx.as<C<T>>();
+  C<T>* t2 = c->kt2.as<C<T>>();
+  int sweeps = 0;
+  bool inner_ok = true;
+  while (e > cfg.tol && sweeps < cfg.max_outer) {
+    int sweep_its = 0;
+    for (int i = 0; i < M; ++i) {
+      const BlockOp<T>& A = ops[i];
+      const long nb = A.nb(), off = (long)A.z0 * nxy;
+      double2* Ri = c->R.as<double2>() + off;
+      double2* Ei = c->E.as<double2>() + off;
+      double rnorm;
+      CKS(norm_c128(c, Ri, c->N, nullptr, 0, nb, &rnorm));
+      if (rnorm == 0.0) continue;
+      // block right-hand side norm |b_i| = |R_i + A_ii E_i| (eqs. 21/23)
+      double bnorm;
+      if (cfg.dd_mode == IE_DD_NONE) {
+        CKS(norm_c128(c, c->E0.as<double2>(), c->N, nullptr, 0, c->N, &bnorm));
+      } else {
+        if (std::is_same<T, float>::value) {
+          CK(launch_c128_to_c64(Ei, c->N, reinterpret_cast<float2*>(dx), nb, nb, s));
+          CKS(A.apply(dx, t2));
+          CKS(norm_c128(c, Ri, c->N, reinterpret_cast<const float2*>(t2), nb, nb, &bnorm));
+        } else {
+          CK(launch_copy_c128(Ei, c->N, reinterpret_cast<double2*>(dx), nb, nb, s));
+          CKS(A.apply(dx, t2));
+          CK(launch_add_c128(Ri, c->N, reinterpret_cast<double2*>(t2), nb, nb, s));
+          CKS(norm_c128(c, reinterpret_cast<const double2*>(t2), nb, nullptr, 0, nb, &bnorm));
+        }
+      }
+      double target = (cfg.dd_mode == IE_DD_NONE) ? cfg.tol : (cfg.adaptive ? e / 10.0 : cfg.fixed_tol);
+      double tol_i = target * bnorm / rnorm;
+      if (std::is_same<T, float>::value) tol_i = std::max(tol_i, cfg.dd_mode == IE_DD_NONE ? 1e-5 : 1e-6);
+      tol_i = std::min(tol_i, 0.5);
+      if (std::is_same<T, float>::value)
+        CK(launch_c128_to_c64(Ri, c->N, reinterpret_cast<float2*>(rhs), nb, nb, s));
+      else
+        CK(launch_copy_c128(Ri, c->N, reinterpret_cast<double2*>(rhs), nb, nb, s));
+      GmresOut go;
+      CKS(gmres<T>(c, A, rhs, dx, true, tol_i, cfg.restart, cfg.max_inner, &go));
+      inner_ok = inner_ok && go.converged;
+      sweep_its += go.iters;
+      info->gmres_iters_total += go.iters;
+      info->matvecs += go.matvecs;
+      if (std::is_same<T, float>::value)
+        CK(launch_add_c64_to_c128(reinterpret_cast<const float2*>(dx), nb, Ei, c->N, nb, s));
+      else
+        CK(launch_add_c128(reinterpret_cast<const double2*>(dx), nb, Ei, c->N, nb, s));
+      if (cfg.dd_mode == IE_DD_GAUSS_SEIDEL) {
+        for (int j = i + 1; j < M; ++j) {  // interaction update of the later blocks (eq. 21)
+          const BlockOp<T>& Bj = ops[j];
+          CKS(conv<T>(c, Sfull, dx, nb, A.z0, A.nz, A.z0, Bj.nz, Bj.z0, EPI_ACCUM128, nullptr, 0, nullptr, 0,
+                      c->R.as<double2>() + (long)Bj.z0 * nxy, c->N, nullptr, 0));
+        }
+      }
+    }
+    sweeps++;
+    CKS(full_residual(c, e0norm, &e));
+    if (record && info->n_history < IE_MAX_HISTORY) {
+      info->sweep_gmres_iters[info->n_history - 1] = sweep_its;
+      info->residual_history[info->n_history++] = e;
+    }
+  }
+  info->outer_iters += sweeps;
+  info->final_rel_residual = std::max(info->final_rel_residual, e);
+  if (e > cfg.tol) return IE_ENOCONV;
+  return IE_OK;
+}
+
+ie_status upload_c128(ie_ctx* c, const double* host, long n, DevBuf& dst) {
+  CK(dst.ensure(sizeof(double2) * n));
+  CK(cudaMemcpyAsync(dst.p, host, sizeof(double2) * n, cudaMemcpyHostToDevice, c->stream));
+  return IE_OK;
+}
+
+}  // namespace
+
+template <typename T>
+ie_status gmres_host(ie_ctx* c, int z0, int nz, const double* b, const double* x0, double tol, int restart,
+                            int max_iter, double* x, int32_t* iters, double* rel) {
+  BlockOp<T> A;
+  CKS(make_block<T>(c, z0, nz, &A));
+  const long n = 3 * A.nb();
+  DevBuf bd, xd, bs, xs;
+  CKS(upload_c128(c, b, n, bd));
+  if (x0) CKS(upload_c128(c, x0, n, xd));
+  else CK(xd.ensure(sizeof(double2) * n));
+  C<T>* bb;
+  C<T>* xx;
+  if (std::is_same<T, float>::value) {
+    CK(bs.ensure(sizeof(float2) * n));
+    CK(xs.ensure(sizeof(float2) * n));
+    const long nb = A.nb();
+    CK(launch_c128_to_c64(bd.as<double2>(), nb, bs.as<float2>(), nb, nb, c->stream));
+    bb = bs.as<C<T>>();
+    xx = xs.as<C<T>>();
+    if (x0) CK(launch_c128_to_c64(xd.as<double2>(), nb, xs.as<float2>(), nb, nb, c->stream));
+  } else {
+    bb = bd.as<C<T>>();
+    xx = xd.as<C<T>>();
+  }
+  GmresOut go;
+  CKS(gmres<T>(c, A, bb, xx, x0 == nullptr, tol, restart, max_iter, &go));
+  if (std::is_same<T, float>::value) {
+    CK(cudaMemsetAsync(xd.p, 0, sizeof(double2) * n, c->stream));
+    CK(launch_add_c64_to_c128(xs.as<float2>(), A.nb(), xd.as<double2>(), A.nb(), A.nb(), c->stream));
+  }
+  CK(cudaMemcpyAsync(x, xd.p, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (iters) *iters = go.iters;
+  if (rel) *rel = go.rel;
+  return go.converged ? IE_OK : IE_ENOCONV;
+}
+
+// =============================================================================== C ABI
+extern "C" {
+
+void ie_default_opts(ie_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->n_blocks = 1;
+  o->z_split = nullptr;
+  o->restart = 30;
+  o->max_outer = 50;
+  o->max_inner = 600;
+  o->precision = IE_PREC_MIXED;
+  o->adaptive = 1;
+  o->fixed_tol = 1e-6;
+}
+
+ie_status ie_create(const ie_grid* grid, double h, double sigma0, double freq, ie_ctx** out) {
+  if (!out) return IE_EINVAL;
+  *out = nullptr;
+  if (!grid || !(h > 0) || !(sigma0 > 0) || !(freq > 0) || !std::isfinite(h) || !std::isfinite(sigma0) ||
+      !std::isfinite(freq))
+    return IE_EINVAL;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nx > 512 || grid->ny > 512 || grid->nz > 512)
+    return IE_EINVAL;
+  auto* c = new (std::nothrow) ie_ctx();
+  if (!c) return IE_ENOMEM;
+  c->nx = grid->nx;
+  c->ny = grid->ny;
+  c->nz = grid->nz;
+  c->N = (long)c->nx * c->ny * c->nz;
+  for (int a = 0; a < 3; ++a) c->origin[a] = grid->origin[a];
+  c->h = h;
+  c->sigma0 = sigma0;
+  c->freq = freq;
+  c->omega = 2.0 * M_PI * freq;
+  const std::complex<double> k = std::sqrt(std::complex<double>(0.0, c->omega * kMu0 * sigma0));
+  c->k0 = make_double2(k.real(), k.imag());
+  const double dv = h * h * h, a = std::cbrt(3.0 * dv / (4.0 * M_PI));
+  const std::complex<double> ika(0.0, 1.0);
+  const std::complex<double> self =
+      ((2.0 / 3.0) * (1.0 - ika * k * a) * std::exp(ika * k * a) - 1.0) / sigma0;  // Section 2.2 self term
+  c->self = make_double2(self.real(), self.imag());
+  c->Lx = next_pow2(2 * c->nx);
+  c->Ly = next_pow2(2 * c->ny);
+  if (!supported_pencil(c->Lx) || !supported_pencil(c->Ly)) {
+    delete c;
+    return IE_EINVAL;
+  }
+  // twiddles exp(-2 pi i k / TWN) in FP64 (angles reduced to the first octant by symmetry)
+  std::vector<double2> t64(TWN);
+  std::vector<float2> t32(TWN);
+  for (int q = 0; q < TWN; ++q) {
+    const double ang = 2.0 * M_PI * (double)q / TWN;
+    const double cr = std::cos(ang), si = std::sin(ang);
+    t64[q] = make_double2(cr, -si);
+    t32[q] = make_float2((float)cr, (float)-si);
+  }
+  if (c->tw64.ensure(sizeof(double2) * TWN) != cudaSuccess || c->tw32.ensure(sizeof(float2) * TWN) != cudaSuccess ||
+      cudaMemcpy(c->tw64.p, t64.data(), sizeof(double2) * TWN, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->tw32.p, t32.data(), sizeof(float2) * TWN, cudaMemcpyHostToDevice) != cudaSuccess ||
+      c->E.ensure(sizeof(double2) * 3 * c->N) != cudaSuccess || c->E0.ensure(sizeof(double2) * 3 * c->N) != cudaSuccess ||
+      c->R.ensure(sizeof(double2) * 3 * c->N) != cudaSuccess || c->ds64.ensure(sizeof(double) * 6 * c->N) != cudaSuccess ||
+      c->ds32.ensure(sizeof(float) * 6 * c->N) != cudaSuccess) {
+    delete c;
+    return IE_ENOMEM;
+  }
+  SpecSet* S = nullptr;
+  if (get_spec(c, c->nz, &S) != IE_OK) {  // whole-grid spectra (FP64 residual, interactions)
+    const ie_status st = c->err.find("alloc") != std::string::npos ? IE_ENOMEM : IE_ECUDA;
+    delete c;
+    return st;
+  }
+  *out = c;
+  return IE_OK;
+}
+
+ie_status ie_set_stream(ie_ctx* c, void* stream) {
+  if (!c) return IE_EINVAL;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  return IE_OK;
+}
+
+static ie_status set_contrast_dev_impl(ie_ctx* c, const double* s6_dev) {
+  CKS(ensure_scalars(c));
+  int* flag = c->flag.as<int>();
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  CK(launch_set_contrast(s6_dev, c->N, c->sigma0, c->ds64.as<double>(), c->ds32.as<float>(), flag, c->stream));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&c->hpin[0], flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::memcpy(&bad, &c->hpin[0], sizeof(int));
+  if (bad) {
+    c->has_contrast = false;
+    return fail(c, IE_EINVAL, "conductivity not finite or not positive definite");
+  }
+  c->has_contrast = true;
+  c->has_field = false;
+  return IE_OK;
+}
+
+ie_status ie_set_contrast(ie_ctx* c, const double* sigma6) {
+  if (!c || !sigma6) return fail(c, IE_EINVAL, "null argument");
+  CK(c->s6_stage.ensure(sizeof(double) * 6 * c->N));
+  CK(cudaMemcpyAsync(c->s6_stage.p, sigma6, sizeof(double) * 6 * c->N, cudaMemcpyHostToDevice, c->stream));
+  return set_contrast_dev_impl(c, c->s6_stage.as<double>());
+}
+
+ie_status ie_set_contrast_dev(ie_ctx* c, const double* sigma6_dev) {
+  if (!c || !sigma6_dev) return fail(c, IE_EINVAL, "null argument");
+  return set_contrast_dev_impl(c, sigma6_dev);
+}
+
+ie_status ie_solve(ie_ctx* c, int32_t n_src, const ie_dipole* src, int32_t n_rx, const double* rx, int32_t dd_mode,
+                   double tol, const ie_opts* opts, double* H_out, ie_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!c) return IE_EINVAL;
+  c->err.clear();
+  if (n_src < 0 || n_rx < 0 || (n_src > 0 && !src) || (n_rx > 0 && (!rx || !H_out)) || !(tol > 0))
+    return fail(c, IE_EINVAL, "bad arguments");
+  if (dd_mode != IE_DD_NONE && dd_mode != IE_DD_JACOBI && dd_mode != IE_DD_GAUSS_SEIDEL)
+    return fail(c, IE_EINVAL, "bad dd_mode");
+  if (!c->has_contrast) return fail(c, IE_ESTATE, "ie_set_contrast has not succeeded");
+  ie_opts o;
+  ie_default_opts(&o);
+  if (opts) o = *opts;
+  SolveCfg cfg;
+  cfg.dd_mode = dd_mode;
+  cfg.restart = o.restart > 0 ? o.restart : 30;
+  cfg.max_outer = o.max_outer > 0 ? o.max_outer : 50;
+  cfg.max_inner = o.max_inner > 0 ? o.max_inner : 20 * cfg.restart;
+  cfg.precision = o.precision;
+  cfg.adaptive = o.adaptive;
+  cfg.fixed_tol = o.fixed_tol > 0 ? o.fixed_tol : tol;
+  cfg.tol = tol;
+  if (cfg.precision != IE_PREC_MIXED && cfg.precision != IE_PREC_FP64) return fail(c, IE_EINVAL, "bad precision");
+  const int M = (dd_mode == IE_DD_NONE) ? 1 : std::max(1, o.n_blocks);
+  if (M > c->nz) return fail(c, IE_EINVAL, "more blocks than z cells");
+  cfg.split.resize(M + 1);
+  if (dd_mode != IE_DD_NONE && o.z_split) {
+    for (int i = 0; i <= M; ++i) cfg.split[i] = o.z_split[i];
+    if (cfg.split[0] != 0 || cfg.split[M] != c->nz) return fail(c, IE_EINVAL, "z_split must run from 0 to nz");
+    for (int i = 0; i < M; ++i)
+      if (cfg.split[i + 1] <= cfg.split[i]) return fail(c, IE_EINVAL, "z_split must increase");
+  } else {
+    for (int i = 0; i <= M; ++i) cfg.split[i] = (int)((long)c->nz * i / M);
+  }
+  for (int q = 0; q < n_src; ++q) CKS(check_point(c, src[q].pos));
+  for (int r = 0; r < n_rx; ++r) CKS(check_point(c, rx + 3 * r));
+  ie_info loc;
+  std::memset(&loc, 0, sizeof(loc));
+  CKS(ensure_scalars(c));
+  if (n_rx > 0) {
+    CK(c->rxdev.ensure(sizeof(double) * 3 * n_rx));
+    CK(c->Hdev.ensure(sizeof(double2) * 3 * n_rx));
+    CK(c->rxpart.ensure(sizeof(double2) * 3 * kMaxRx * receivers_partials_blocks(c->N)));
+    CK(cudaMemcpyAsync(c->rxdev.p, rx, sizeof(double) * 3 * n_rx, cudaMemcpyHostToDevice, c->stream));
+  }
+  ie_status worst = IE_OK;
+  for (int q = 0; q < n_src; ++q) {
+    CK(launch_incident_E(c->E0.as<double2>(), c->nx, c->ny, c->nz, c->origin, c->h, src[q].pos, src[q].moment, c->k0,
+                         c->omega * kMu0, c->stream));
+    ie_status st = cfg.precision == IE_PREC_FP64 ? solve_one<double>(c, cfg, &loc, q == 0)
+                                                 : solve_one<float>(c, cfg, &loc, q == 0);
+    if (st != IE_OK && st != IE_ENOCONV) return st;
+    if (st == IE_ENOCONV) worst = IE_ENOCONV;
+    c->has_field = true;
+    for (int r0 = 0; r0 < n_rx; r0 += kMaxRx) {
+      const int nr = std::min(kMaxRx, n_rx - r0);
+      CK(launch_receivers(c->E.as<double2>(), c->N, c->ds64.as<double>(), c->N, c->nx, c->ny, c->origin, c->h,
+                          c->rxdev.as<double>() + 3 * r0, nr, c->k0, c->rxpart.as<double2>(), src[q].pos,
+                          src[q].moment, c->Hdev.as<double2>() + 3 * r0, c->stream));
+    }
+    if (n_rx > 0) {
+      CK(cudaMemcpyAsync(H_out + (size_t)q * n_rx * 6, c->Hdev.p, sizeof(double2) * 3 * n_rx, cudaMemcpyDeviceToHost,
+                         c->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  loc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = loc;
+  if (worst == IE_ENOCONV) c->err = "tolerance not reached within the iteration limits";
+  return worst;
+}
+
+ie_status ie_get_field(ie_ctx* c, double* E_out) {
+  if (!c || !E_out) return fail(c, IE_EINVAL, "null argument");
+  if (!c->has_field) return fail(c, IE_ESTATE, "no solve has run");
+  CK(cudaMemcpyAsync(E_out, c->E.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return IE_OK;
+}
+
+ie_status ie_matvec(ie_ctx* c, int32_t precision, int32_t z0, int32_t nz, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, IE_EINVAL, "null argument");
+  const long nb = (long)nz * c->ny * c->nx;
+  DevBuf xd, yd, xs, ys;
+  CKS(upload_c128(c, x, 3 * std::max(nb, 0L), xd));
+  if (precision == IE_PREC_FP64) {
+    BlockOp<double> A;
+    CKS(make_block<double>(c, z0, nz, &A));
+    CK(yd.ensure(sizeof(double2) * 3 * nb));
+    CKS(A.apply(xd.as<double2>(), yd.as<double2>()));
+    CK(cudaMemcpyAsync(y, yd.p, sizeof(double2) * 3 * nb, cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    BlockOp<float> A;
+    CKS(make_block<float>(c, z0, nz, &A));
+    CK(xs.ensure(sizeof(float2) * 3 * nb));
+    CK(ys.ensure(sizeof(float2) * 3 * nb));
+    CK(yd.ensure(sizeof(double2) * 3 * nb));
+    CK(launch_c128_to_c64(xd.as<double2>(), nb, xs.as<float2>(), nb, nb, c->stream));
+    CKS(A.apply(xs.as<float2>(), ys.as<float2>()));
+    CK(cudaMemsetAsync(yd.p, 0, sizeof(double2) * 3 * nb, c->stream));
+    CK(launch_add_c64_to_c128(ys.as<float2>(), nb, yd.as<double2>(), nb, nb, c->stream));
+    CK(cudaMemcpyAsync(y, yd.p, sizeof(double2) * 3 * nb, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return IE_OK;
+}
+
+ie_status ie_matvec_dev(ie_ctx* c, int32_t z0, int32_t nz, const void* x_dev, void* y_dev) {
+  if (!c || !x_dev || !y_dev || x_dev == y_dev) return fail(c, IE_EINVAL, "bad argument");
+  BlockOp<float> A;
+  CKS(make_block<float>(c, z0, nz, &A));
+  return A.apply(reinterpret_cast<const float2*>(x_dev), reinterpret_cast<float2*>(y_dev));
+}
+
+ie_status ie_interaction(ie_ctx* c, int32_t zs0, int32_t nzs, int32_t zt0, int32_t nzt, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, IE_EINVAL, "null argument");
+  if (zs0 < 0 || nzs < 1 || zs0 + nzs > c->nz || zt0 < 0 || nzt < 1 || zt0 + nzt > c->nz)
+    return fail(c, IE_EINVAL, "slab outside the grid");
+  if (!c->has_contrast) return fail(c, IE_ESTATE, "no contrast set");
+  SpecSet* S = nullptr;
+  CKS(get_spec(c, c->nz, &S));
+  const long nxy = (long)c->nx * c->ny, ns = nzs * nxy, nt = nzt * nxy;
+  DevBuf xd, yd;
+  CKS(upload_c128(c, x, 3 * ns, xd));
+  CK(yd.ensure(sizeof(double2) * 3 * nt));
+  CKS(conv<double>(c, S, xd.as<double2>(), ns, zs0, nzs, zs0, nzt, zt0, EPI_CONV, nullptr, 0, yd.as<double2>(), nt,
+                   nullptr, 0, nullptr, 0));
+  CK(cudaMemcpyAsync(y, yd.p, sizeof(double2) * 3 * nt, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return IE_OK;
+}
+
+ie_status ie_gmres(ie_ctx* c, int32_t precision, int32_t z0, int32_t nz, const double* b, const double* x0, double tol,
+                   int32_t restart, int32_t max_iter, double* x, int32_t* iters, double* rel) {
+  if (!c || !b || !x || !(tol > 0) || max_iter < 0) return fail(c, IE_EINVAL, "bad argument");
+  return precision == IE_PREC_FP64 ? gmres_host<double>(c, z0, nz, b, x0, tol, restart, max_iter, x, iters, rel)
+                                   : gmres_host<float>(c, z0, nz, b, x0, tol, restart, max_iter, x, iters, rel);
+}
+
+ie_status ie_green_spectrum(ie_ctx* c, int32_t nz_set, int32_t comp, double* out, int32_t* dims) {
+  if (!c || !out || comp < 0 || comp > 5 || nz_set < 1 || nz_set > c->nz) return fail(c, IE_EINVAL, "bad argument");
+  SpecSet* S = nullptr;
+  CKS(get_spec(c, nz_set, &S));
+  const long ocs = (long)(c->Lx / 2 + 1) * (c->Ly / 2 + 1) * (S->Lz / 2 + 1);
+  CK(cudaMemcpyAsync(out, S->G64.as<double2>() + comp * ocs, sizeof(double2) * ocs, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (dims) {
+    dims[0] = c->Lx;
+    dims[1] = c->Ly;
+    dims[2] = S->Lz;
+  }
+  return IE_OK;
+}
+
+ie_status ie_incident_field(ie_ctx* c, const ie_dipole* src, double* E0_out) {
+  if (!c || !src || !E0_out) return fail(c, IE_EINVAL, "null argument");
+  CKS(check_point(c, src->pos));
+  DevBuf e;
+  CK(e.ensure(sizeof(double2) * 3 * c->N));
+  CK(launch_incident_E(e.as<double2>(), c->nx, c->ny, c->nz, c->origin, c->h, src->pos, src->moment, c->k0,
+                       c->omega * kMu0, c->stream));
+  CK(cudaMemcpyAsync(E0_out, e.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return IE_OK;
+}
+
+ie_status ie_receiver_fields(ie_ctx* c, const double* E, const ie_dipole* src, int32_t n_rx, const double* rx,
+                             double* H_out) {
+  if (!c || !E || !src || (n_rx > 0 && (!rx || !H_out)) || n_rx < 0) return fail(c, IE_EINVAL, "bad argument");
+  if (!c->has_contrast) return fail(c, IE_ESTATE, "no contrast set");
+  for (int r = 0; r < n_rx; ++r) CKS(check_point(c, rx + 3 * r));
+  if (n_rx == 0) return IE_OK;
+  DevBuf ed, rxd, hd, pd;
+  CKS(upload_c128(c, E, 3 * c->N, ed));
+  CK(rxd.ensure(sizeof(double) * 3 * n_rx));
+  CK(hd.ensure(sizeof(double2) * 3 * n_rx));
+  CK(pd.ensure(sizeof(double2) * 3 * kMaxRx * receivers_partials_blocks(c->N)));
+  CK(cudaMemcpyAsync(rxd.p, rx, sizeof(double) * 3 * n_rx, cudaMemcpyHostToDevice, c->stream));
+  for (int r0 = 0; r0 < n_rx; r0 += kMaxRx) {
+    const int nr = std::min(kMaxRx, n_rx - r0);
+    CK(launch_receivers(ed.as<double2>(), c->N, c->ds64.as<double>(), c->N, c->nx, c->ny, c->origin, c->h,
+                        rxd.as<double>() + 3 * r0, nr, c->k0, pd.as<double2>(), src->pos, src->moment,
+                        hd.as<double2>() + 3 * r0, c->stream));
+  }
+  CK(cudaMemcpyAsync(H_out, hd.p, sizeof(double2) * 3 * n_rx, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return IE_OK;
+}
+
+ie_status ie_fft_dims(const ie_ctx* c, int32_t nz_set, int32_t* dims) {
+  if (!c || !dims || nz_set < 1) return IE_EINVAL;
+  dims[0] = c->Lx;
+  dims[1] = c->Ly;
+  dims[2] = next_pow2(2 * nz_set);
+  return IE_OK;
+}
+
+const char* ie_last_error(const ie_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void ie_destroy(ie_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  delete c;
+}
+
+}  // extern "C"
