@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the IE forward model (one solve = one step) on the 128x128x256 two-sub-domain workload.
+
+Workload (the paper's logging window 1 shape, Section 3.3): 128 x 128 x 256 cells of 0.25 m split
+into two 128^3 sub-domains along z, block Gauss-Seidel with the adaptive sub-domain tolerance e/10
+(Algorithm 1), complex64 FFT convolution and Krylov vectors with FP64 whole-grid residual and
+refinement, target e <= 1e-6 (eq. 9) verified in FP64; five dipping TI layers (anisotropy ratio
+1-10, Appendix C rotation) plus two isotropic ellipsoids, seeded; coaxial z magnetic dipole with
+receivers at 0.5/1/2 m; f = 400 kHz, sigma0 = 0.1 S/m. Synthetic data: the paper's formations
+exist only in figures.
+
+One step = ie_set_contrast_dev + ie_solve (incident field, Algorithm 1, receivers). The Green
+spectra (ie_create) depend only on the grid, cell size, background and frequency and are computed
+once before the timed region, as the paper precomputes them (Section 2.2). Inputs (fields 200 MB,
+Krylov basis 1.5 GB per sub-domain solve) are larger than the 129 MB L2.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IE forward solves/sec at 1e-6 rel. residual; matvec HBM GB/s vs peak"
+UNIT = "solves/s"
+WORKLOAD = "DD 128x128x256 @0.25 m, 2 sub-domains block Gauss-Seidel adaptive (GS-A), 5 dipping TI layers + 2 ellipsoids, 1 coaxial tool position, 400 kHz, tol 1e-6"
+# Operator applications of one oracle-sized solve, used only to scale the CPU oracle sample of the
+# reference arm to solves/s (the GB300 arm counts them live, "CPU baseline").
+REF_BLOCK_APPLICATIONS_PER_SOLVE = 2000
+REF_FULL_APPLICATIONS_PER_SOLVE = 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--scale", type=int, default=1, help="divide the grid by this factor (testing only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel_class: str):
+    """Per-launch DRAM traffic of a kernel from the committed ncu summary, or None when the kernel
+    source changed since the capture (the summary stores a hash of the sources it covers)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    import hashlib
+
+    rec = json.load(open(p)).get(kernel_class)
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != rec["sha256"]:
+        return None
+    return rec
+
+
+# ------------------------------------------------------------------------------------ CPU oracle
+def oracle_block_sample(wl, z0, nz, n_apply=1):
+    """Time the CPU oracle's operator of one sub-domain: spectra setup + n_apply applications."""
+    import numpy as np
+
+    from oracle import operator as oop
+
+    t0 = time.perf_counter()
+    dsig = oop.contrast(wl.sigma6[z0:z0 + nz], wl.sigma0)
+    op = oop.FFTOperator(dsig, wl.grid.h, wl.freq, wl.sigma0)
+    t1 = time.perf_counter()
+    x = np.ones((3, nz, wl.grid.ny, wl.grid.nx), dtype=np.complex128)
+    for _ in range(n_apply):
+        x = op(x)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / n_apply
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------------------------ GB300 arm
+def run_gb300(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2306_17537_gb300 import ie, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    # weak scaling: every rank solves its own tool position (independent model seed), no data exchange
+    wl = inputs.config2(args.seed + rank, scale=args.scale)
+    g = wl.grid
+    t_setup0 = time.perf_counter()
+    ctx = ie.Context(g, g.h, wl.sigma0, wl.freq)
+    stream = torch.cuda.current_stream(dev)
+    ctx.set_stream(stream)
+    setup_s = time.perf_counter() - t_setup0
+    s6_dev = torch.from_numpy(np.ascontiguousarray(wl.sigma6)).to(dev)
+    opts = ie.make_opts(z_split=wl.z_split, restart=wl.restart, precision=ie.IE_PREC_MIXED, max_inner=4000,
+                        max_outer=60)
+    src, rx = wl.sources, wl.receivers
+
+    def step_dev():
+        ctx.set_contrast_dev(s6_dev)
+        return ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, opts)
+
+    for _ in range(args.warmup):
+        H, info, st = step_dev()
+    # ----------------------------------------------------------------- timed region (device inputs)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ctx.profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        H, info, st = step_dev()
+        infos.append(info)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    tmax = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    t_ms_max = float(tmax.item())
+    value = args.steps * world / (t_ms_max / 1000.0)
+    # ----------------------------------------------------------------- end to end (host buffers)
+    s6_pin = torch.from_numpy(np.ascontiguousarray(wl.sigma6)).pin_memory()
+    s6_host = s6_pin.numpy()
+    e2e_steps = max(1, min(args.steps, 2))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        ctx.set_contrast(s6_host)
+        H2, info2, _ = ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, opts)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    te = torch.tensor([e0.elapsed_time(e1)], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = e2e_steps * world / (float(te.item()) / 1000.0)
+    h2d = s6_host.nbytes + rx.nbytes + 48 * len(src)
+    d2h = H2.nbytes
+    # ----------------------------------------------------------------- block operator bandwidth
+    nb = 3 * (g.nz // 2) * g.ny * g.nx
+    x = torch.randn(nb, dtype=torch.complex64, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        ctx.matvec_dev(x, y, z0=0, nz=g.nz // 2)
+    torch.cuda.synchronize(dev)
+    ctx.profile_enable(True)
+    reps = 20
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(reps):
+        ctx.matvec_dev(x, y, z0=0, nz=g.nz // 2)
+    m1.record(stream)
+    torch.cuda.synchronize(dev)
+    mv_ms = m0.elapsed_time(m1) / reps
+    mprof = ctx.profile_read()
+    ctx.profile_enable(False)
+    mv_bytes = sum(mprof[k][2] for k in ("P1_c64", "P2_c64", "P3_c64", "P4_c64", "P5_c64")) / reps
+    n_block = (g.nz // 2) * g.ny * g.nx
+    peak, peak_kind = measured_peaks()
+    # ----------------------------------------------------------------- roofline of the dominant kernel
+    dom = max(prof, key=lambda k: prof[k][1])
+    launches, ms, by = prof[dom]
+    achieved = (by / 1e9) / (ms / 1e3) if ms > 0 else 0.0
+    tr = traffic_record(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                "algorithmic_bytes_per_launch": by / max(launches, 1), "avg_launch_us": 1e3 * ms / max(launches, 1),
+                "launches": launches}
+    total_ms = sum(v[1] for v in prof.values())
+    breakdown = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_ms, 4) if total_ms else 0,
+                     "GBps": round((v[2] / 1e9) / (v[1] / 1e3), 1) if v[1] > 0 else None}
+                 for k, v in prof.items() if v[0] > 0}
+    gpu_launches = int(sum(v[0] for v in prof.values()))
+    last = infos[-1]
+    # ----------------------------------------------------------------- CPU oracle baseline
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_setup, t_apply = oracle_block_sample(wl, 0, g.nz // 2, n_apply=1)
+        # whole-grid applications (FP64 residual) cost about twice a sub-domain one (twice the volume)
+        applications = last.matvecs + 2 * (last.outer_iters + 1) + last.outer_iters
+        est = 3 * t_setup + t_apply * applications
+        cpu_baseline = {"value": 1.0 / est, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                        "sample": (f"CPU FP64 oracle: spectra of one 128^3 sub-domain ({t_setup:.1f} s) + one operator "
+                                   f"application ({t_apply:.1f} s), scaled to this solve's {applications} "
+                                   f"sub-domain-operator equivalents (GMRES applications + 2x per FP64 residual + "
+                                   f"interaction updates) and 3 spectra setups"),
+                        "seconds_per_solve_estimate": est}
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_ms_max / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic (seeded generator)",
+        "config": {"workload": WORKLOAD, "grid": [g.nx, g.ny, g.nz], "h_m": g.h, "sub_domains": wl.z_split,
+                   "dd": "block Gauss-Seidel, adaptive tol e/10", "precision": "complex64 conv/Krylov + FP64 refinement",
+                   "restart": wl.restart, "tol": wl.tol, "freq_hz": wl.freq, "sigma0": wl.sigma0, "seed": args.seed,
+                   "setup_s_excluded": round(setup_s, 3), "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"{world} independent tool positions (one per GPU)"},
+        "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "roofline": roofline,
+        "matvec": {"sub_domain": [g.nx, g.ny, g.nz // 2], "ms": round(mv_ms, 4),
+                   "algorithmic_GB": round(mv_bytes / 1e9, 4), "GBps": round(mv_bytes / 1e9 / (mv_ms / 1e3), 1),
+                   "frac_of_peak": round(mv_bytes / 1e9 / (mv_ms / 1e3) / peak, 4),
+                   "bytes_per_voxel": round(mv_bytes / n_block, 1)},
+        "solve": {"status": int(st), "outer_iters": last.outer_iters, "gmres_iters": last.gmres_iters_total,
+                  "matvecs": last.matvecs, "final_rel_residual": last.final_rel_residual,
+                  "residual_history": [float(v) for v in last.history()],
+                  "H_rx_z": [[float(H[0, r, 2].real), float(H[0, r, 2].imag)] for r in range(H.shape[1])]},
+        "kernels": breakdown,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "cpu_baseline": cpu_baseline,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The CPU FP64 oracle as the reference: each step times one bounded sample (one application of
+    the 128^3 sub-domain operator) and converts it to solves/s with a fixed operator-application count."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2306_17537_gb300 import inputs
+
+    import numpy as np
+
+    from oracle import operator as oop
+
+    wl = inputs.config2(args.seed, scale=args.scale)
+    t0 = time.perf_counter()
+    dsig = oop.contrast(wl.sigma6[: wl.grid.nz // 2], wl.sigma0)
+    op = oop.FFTOperator(dsig, wl.grid.h, wl.freq, wl.sigma0)
+    t_setup = time.perf_counter() - t0
+    x = np.ones((3, wl.grid.nz // 2, wl.grid.ny, wl.grid.nx), dtype=np.complex128)
+    for _ in range(min(args.warmup, 1)):
+        op(x)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        op(x)
+        times.append(time.perf_counter() - t0)
+    t_apply = sum(times) / len(times)
+    applications = REF_BLOCK_APPLICATIONS_PER_SOLVE + 2 * REF_FULL_APPLICATIONS_PER_SOLVE
+    est = 3 * t_setup + t_apply * applications
+    value = 1.0 / est
+    sample = (f"one application of the CPU FP64 oracle's 128^3 sub-domain operator per step (mean {t_apply:.2f} s) "
+              f"+ spectra setup ({t_setup:.1f} s), scaled to {applications} sub-domain-operator equivalents per solve")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * t_apply, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded generator)",
+           "config": {"workload": WORKLOAD, "seed": args.seed}, "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gb300(a)

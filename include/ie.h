@@ -167,6 +167,30 @@ ie_status ie_receiver_fields(ie_ctx* ctx, const double* E, const ie_dipole* src,
 /* Padded FFT lengths (Lx, Ly, Lz) the context uses for a slab of nz_set cells. */
 ie_status ie_fft_dims(const ie_ctx* ctx, int32_t nz_set, int32_t* dims_out);
 
+/* Kernel classes for the built-in launch accounting (see ie_profile_enable). */
+typedef enum {
+  IE_K_P1_C64 = 0,  /* contrast product + x-FFT (complex64) */
+  IE_K_P2_C64 = 1,  /* y-FFT (complex64) */
+  IE_K_P3_C64 = 2,  /* z-FFT + Green product + inverse z-FFT (complex64) */
+  IE_K_P4_C64 = 3,  /* inverse y-FFT (complex64) */
+  IE_K_P5_C64 = 4,  /* inverse x-FFT + crop + combine (complex64) */
+  IE_K_P1_C128 = 5, IE_K_P2_C128 = 6, IE_K_P3_C128 = 7, IE_K_P4_C128 = 8, IE_K_P5_C128 = 9,
+  IE_K_DOTS = 10,        /* Arnoldi inner products */
+  IE_K_UPDATE = 11,      /* Arnoldi vector updates */
+  IE_K_KRYLOV_MISC = 12, /* reductions, scaling, basis combination, norms */
+  IE_K_FIELD = 13,       /* incident field, receivers, contrast, field copies */
+  IE_K_SETUP = 14,       /* Green tabulation and spectra */
+  IE_K_COUNT = 15
+} ie_kernel_class;
+
+/* Launch accounting. Every kernel launch is always counted per class together with its algorithmic
+ * bytes (the HBM bytes the pass model says it must move). With on != 0, each launch is also
+ * bracketed by CUDA events on the context stream and its device time accumulated. Resets counters. */
+ie_status ie_profile_enable(ie_ctx* ctx, int32_t on);
+/* Counters of one class since the last ie_profile_enable: launches, device milliseconds (0 unless
+ * timing was on) and algorithmic bytes. Any output pointer may be NULL. */
+ie_status ie_profile_read(const ie_ctx* ctx, int32_t kclass, int64_t* launches, double* ms, double* algo_bytes);
+
 /* Last error message of the context (never NULL; "" when none). */
 const char* ie_last_error(const ie_ctx* ctx);
 

@@ -91,9 +91,19 @@ struct ie_ctx {
   DevBuf part, dh, dh2, dnrm, dy, flag, rxdev, Hdev, rxpart;
   double2* hpin = nullptr;  // pinned host scratch for small reductions
 
+  struct Prof {  // launch accounting (ie_profile_enable / ie_profile_read)
+    bool on = false;
+    int64_t launches[IE_K_COUNT] = {};
+    double ms[IE_K_COUNT] = {}, bytes[IE_K_COUNT] = {};
+    std::vector<cudaEvent_t> ev;  // event pairs, reused
+    std::vector<int> cls;
+    size_t used = 0;
+  } prof;
+
   ~ie_ctx() {
     for (auto* s : specs) delete s;
     if (hpin) cudaFreeHost(hpin);
+    for (auto e : prof.ev) cudaEventDestroy(e);
   }
 };
 
@@ -117,6 +127,51 @@ ie_status fail(ie_ctx* c, ie_status st, const std::string& msg) {
     ie_status _s = (expr);        \
     if (_s != IE_OK) return _s;   \
   } while (0)
+
+// Launch with accounting: counts the launch and its algorithmic bytes in class `cls` and, when timing
+// is on, brackets it with a pair of CUDA events on the context stream.
+template <class F> cudaError_t kl(ie_ctx* c, int cls, double bytes, F&& f) {
+  auto& P = c->prof;
+  P.launches[cls]++;
+  P.bytes[cls] += bytes;
+  if (!P.on) return f();
+  if (2 * P.used + 2 > P.ev.size()) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return e;
+    P.ev.push_back(a);
+    P.ev.push_back(b);
+    P.cls.push_back(0);
+  }
+  cudaEvent_t a = P.ev[2 * P.used], b = P.ev[2 * P.used + 1];
+  cudaError_t e = cudaEventRecord(a, c->stream);
+  if (e == cudaSuccess) e = f();
+  if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+  if (e == cudaSuccess) P.cls[P.used++] = cls;
+  return e;
+}
+#define KL(cls, bytes, expr) CK(kl(c, (cls), (double)(bytes), [&]() -> cudaError_t { return (expr); }))
+
+// Fold completed event pairs into the per-class times (call only after the stream has drained).
+cudaError_t drain(ie_ctx* c) {
+  auto& P = c->prof;
+  for (size_t k = 0; k < P.used; ++k) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(P.ev[2 * k + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, P.ev[2 * k], P.ev[2 * k + 1]);
+    if (e != cudaSuccess) return e;
+    P.ms[P.cls[k]] += ms;
+  }
+  P.used = 0;
+  return cudaSuccess;
+}
+cudaError_t sync(ie_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? drain(c) : e;
+}
+
+template <typename T> constexpr int cls_base() { return std::is_same<T, float>::value ? IE_K_P1_C64 : IE_K_P1_C128; }
 
 template <typename T> const C<T>* twid(const ie_ctx* c);
 template <> const float2* twid<float>(const ie_ctx* c) { return c->tw32.as<float2>(); }
@@ -153,24 +208,35 @@ ie_status get_spec(ie_ctx* c, int nz_set, SpecSet** out) {
   double2* F = full.as<double2>();
   const double2* tw = c->tw64.as<double2>();
   for (int comp = 0; comp < 6; ++comp) {
-    cudaError_t e = launch_green_tab(F, comp, c->Lx, c->Ly, Lz, c->nx, c->ny, nz_set, c->h, c->k0, c->sigma0, c->self,
-                                     c->stream);
-    if (e == cudaSuccess) e = ConvLaunch<double>::rows(c->Lx, -1, F, (long)Lz * c->Ly, tw, c->stream);
-    if (e == cudaSuccess)  // y: element e of lane x in plane z at z*Ly*Lx + e*Lx + x
-      e = ConvLaunch<double>::lanes(c->Ly, -1, F, 0, (long)c->Ly * c->Lx, c->Lx, c->Ly, F, 0, (long)c->Ly * c->Lx,
-                                    c->Lx, c->Ly, c->Lx, Lz, 1, tw, c->stream);
-    if (e == cudaSuccess)  // z: element e of lane x in row y at y*Lx + e*Ly*Lx + x
-      e = ConvLaunch<double>::lanes(Lz, -1, F, 0, c->Lx, (long)c->Ly * c->Lx, Lz, F, 0, c->Lx, (long)c->Ly * c->Lx, Lz,
-                                    c->Lx, c->Ly, 1, tw, c->stream);
+    const double vol = (double)Lz * c->Ly * c->Lx;
+    cudaError_t e = kl(c, IE_K_SETUP, 16.0 * vol, [&]() {
+      return launch_green_tab(F, comp, c->Lx, c->Ly, Lz, c->nx, c->ny, nz_set, c->h, c->k0, c->sigma0, c->self,
+                              c->stream);
+    });
     if (e == cudaSuccess)
-      e = launch_extract_octant(F, c->Lx, c->Ly, Lz, scale, S->G64.as<double2>() + comp * ocs,
-                                S->G32.as<float2>() + comp * ocs, c->stream);
+      e = kl(c, IE_K_SETUP, 32.0 * vol,
+             [&]() { return ConvLaunch<double>::rows(c->Lx, -1, F, (long)Lz * c->Ly, tw, c->stream); });
+    if (e == cudaSuccess)  // y: element e of lane x in plane z at z*Ly*Lx + e*Lx + x
+      e = kl(c, IE_K_SETUP, 32.0 * vol, [&]() {
+        return ConvLaunch<double>::lanes(c->Ly, -1, F, 0, (long)c->Ly * c->Lx, c->Lx, c->Ly, F, 0,
+                                         (long)c->Ly * c->Lx, c->Lx, c->Ly, c->Lx, Lz, 1, tw, c->stream);
+      });
+    if (e == cudaSuccess)  // z: element e of lane x in row y at y*Lx + e*Ly*Lx + x
+      e = kl(c, IE_K_SETUP, 32.0 * vol, [&]() {
+        return ConvLaunch<double>::lanes(Lz, -1, F, 0, c->Lx, (long)c->Ly * c->Lx, Lz, F, 0, c->Lx,
+                                         (long)c->Ly * c->Lx, Lz, c->Lx, c->Ly, 1, tw, c->stream);
+      });
+    if (e == cudaSuccess)
+      e = kl(c, IE_K_SETUP, 16.0 * ocs + 24.0 * ocs, [&]() {
+        return launch_extract_octant(F, c->Lx, c->Ly, Lz, scale, S->G64.as<double2>() + comp * ocs,
+                                     S->G32.as<float2>() + comp * ocs, c->stream);
+      });
     if (e != cudaSuccess) {
       delete S;
       return fail(c, IE_ECUDA, std::string("Green spectra: ") + cudaGetErrorString(e));
     }
   }
-  cudaError_t e = cudaStreamSynchronize(c->stream);  // `full` is freed on return
+  cudaError_t e = sync(c);  // `full` is freed on return
   if (e != cudaSuccess) {
     delete S;
     return fail(c, IE_ECUDA, std::string("Green spectra: ") + cudaGetErrorString(e));
@@ -206,13 +272,22 @@ ie_status conv(ie_ctx* c, const SpecSet* S, const C<T>* x, long x_cs, int zs0, i
   const long nxy = (long)c->nx * c->ny;
   const C<T>* tw = twid<T>(c);
   cudaStream_t s = c->stream;
-  CK(ConvLaunch<T>::p1(c->Lx, x, x_cs, dsig<T>(c) + (long)zs0 * nxy, c->N, A, A_cs, c->nx, (long)nzs * c->ny, tw, s));
-  CK(ConvLaunch<T>::lanes(c->Ly, -1, A, A_cs, (long)c->ny * c->Lx, c->Lx, c->ny, B, B_cs, (long)c->Ly * c->Lx, c->Lx,
+  // algorithmic bytes of the pass model: every pass reads and writes its operands exactly once
+  const double sz = sizeof(C<T>), ocs = (double)(c->Lx / 2 + 1) * (c->Ly / 2 + 1) * (S->Lz / 2 + 1);
+  const double epi = mode == EPI_APPLY ? 2 * sz : mode == EPI_CONV ? sz : mode == EPI_ACCUM128 ? 32.0 : 32.0 + sz;
+  const int k0 = cls_base<T>();
+  KL(k0 + 0, (3 * sz + 6 * sizeof(T)) * nzs * nxy + 3 * sz * nzs * c->ny * c->Lx,
+     ConvLaunch<T>::p1(c->Lx, x, x_cs, dsig<T>(c) + (long)zs0 * nxy, c->N, A, A_cs, c->nx, (long)nzs * c->ny, tw, s));
+  KL(k0 + 1, 3 * sz * nzs * c->Lx * (double)(c->ny + c->Ly),
+     ConvLaunch<T>::lanes(c->Ly, -1, A, A_cs, (long)c->ny * c->Lx, c->Lx, c->ny, B, B_cs, (long)c->Ly * c->Lx, c->Lx,
                           c->Ly, c->Lx, nzs, 3, tw, s));
-  CK(ConvLaunch<T>::p3(S->Lz, B, B_cs, nzs, os, B, B_cs, nzt, ot, spec<T>(S), c->Lx, c->Ly, tw, s));
-  CK(ConvLaunch<T>::lanes(c->Ly, +1, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx, c->Lx,
+  KL(k0 + 2, 3 * sz * (double)(nzs + nzt) * c->Ly * c->Lx + 6 * sz * ocs,
+     ConvLaunch<T>::p3(S->Lz, B, B_cs, nzs, os, B, B_cs, nzt, ot, spec<T>(S), c->Lx, c->Ly, tw, s));
+  KL(k0 + 3, 3 * sz * nzt * c->Lx * (double)(c->Ly + c->ny),
+     ConvLaunch<T>::lanes(c->Ly, +1, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx, c->Lx,
                           c->ny, c->Lx, nzt, 3, tw, s));
-  CK(ConvLaunch<T>::p5(c->Lx, mode, A, A_cs, c->nx, (long)nzt * c->ny, xin, xin_cs, y, y_cs, r, r_cs, b, b_cs, tw, s));
+  KL(k0 + 4, 3 * sz * nzt * c->ny * c->Lx + 3 * epi * nzt * nxy,
+     ConvLaunch<T>::p5(c->Lx, mode, A, A_cs, c->nx, (long)nzt * c->ny, xin, xin_cs, y, y_cs, r, r_cs, b, b_cs, tw, s));
   return IE_OK;
 }
 
@@ -249,15 +324,15 @@ ie_status ensure_scalars(ie_ctx* c) {
 
 // FP64 sum of partials -> host
 ie_status reduce_to_host(ie_ctx* c, const double2* part, int nblk, int nk, double2* host) {
-  CK(launch_reduce(part, nblk, nk, c->dh2.as<double2>(), nullptr, nullptr, c->stream));
+  KL(IE_K_KRYLOV_MISC, 16.0 * nk * nblk, launch_reduce(part, nblk, nk, c->dh2.as<double2>(), nullptr, nullptr, c->stream));
   CK(cudaMemcpyAsync(c->hpin, c->dh2.as<double2>(), sizeof(double2) * nk, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(sync(c));
   std::memcpy(host, c->hpin, sizeof(double2) * nk);
   return IE_OK;
 }
 
 template <typename T> ie_status vnorm(ie_ctx* c, const C<T>* v, long n, double* out) {
-  CK(Krylov<T>::norm2(v, n, c->part.as<double2>(), c->stream));
+  KL(IE_K_KRYLOV_MISC, sizeof(C<T>) * (double)n, Krylov<T>::norm2(v, n, c->part.as<double2>(), c->stream));
   double2 h;
   CKS(reduce_to_host(c, c->part.as<double2>(), krylov_blocks(n), 1, &h));
   *out = std::sqrt(std::max(h.x, 0.0));
@@ -265,7 +340,7 @@ template <typename T> ie_status vnorm(ie_ctx* c, const C<T>* v, long n, double* 
 }
 
 ie_status norm_c128(ie_ctx* c, const double2* a, long a_cs, const float2* b, long b_cs, long n, double* out) {
-  CK(launch_norm2_c128(a, a_cs, b, b_cs, n, c->part.as<double2>(), c->stream));
+  KL(IE_K_FIELD, (16.0 + (b ? 8.0 : 0.0)) * 3 * n, launch_norm2_c128(a, a_cs, b, b_cs, n, c->part.as<double2>(), c->stream));
   double2 h;
   CKS(reduce_to_host(c, c->part.as<double2>(), kRedBlocks, 1, &h));
   *out = std::sqrt(std::max(h.x, 0.0));
@@ -273,7 +348,7 @@ ie_status norm_c128(ie_ctx* c, const double2* a, long a_cs, const float2* b, lon
 }
 
 struct GmresOut {
-  int iters = 0, matvecs = 0;
+  int iters = 0, matvecs = 0, reorth = 0;
   double rel = 0;
   bool converged = false;
 };
@@ -311,12 +386,12 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
   double beta;
   if (x0_zero) {
     CK(cudaMemsetAsync(x, 0, sizeof(C<T>) * n, s));
-    CK(Krylov<T>::scale(b, V, n, nullptr, 1.0 / bnorm, s));
+    KL(IE_K_KRYLOV_MISC, 2.0 * sizeof(C<T>) * n, Krylov<T>::scale(b, V, n, nullptr, 1.0 / bnorm, s));
     beta = bnorm;
   } else {
     CKS(A.apply(x, tmp));
     out->matvecs++;
-    CK(Krylov<T>::rsub(b, tmp, n, part, s));
+    KL(IE_K_KRYLOV_MISC, 3.0 * sizeof(C<T>) * n, Krylov<T>::rsub(b, tmp, n, part, s));
     double2 h;
     CKS(reduce_to_host(c, part, krylov_blocks(n), 1, &h));
     beta = std::sqrt(std::max(h.x, 0.0));
@@ -325,7 +400,7 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
       out->converged = true;
       return IE_OK;
     }
-    CK(Krylov<T>::scale(tmp, V, n, nullptr, 1.0 / beta, s));
+    KL(IE_K_KRYLOV_MISC, 2.0 * sizeof(C<T>) * n, Krylov<T>::scale(tmp, V, n, nullptr, 1.0 / beta, s));
   }
   out->rel = beta / bnorm;
   const int nblk = krylov_blocks(n);
@@ -342,19 +417,30 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
       CKS(A.apply(V + (size_t)j * n, w));
       out->matvecs++;
       const int nv = j + 1;
-      CK(Krylov<T>::dots(V, n, nv, w, n, part, true, nullptr, s));
-      CK(launch_reduce(part, nblk, nv + 1, dh, nullptr, nullptr, s));  // dh[0..j] = V^H w, dh[nv] = |w|^2
-      CK(Krylov<T>::update(V, n, nv, dh, w, n, part, nullptr, s));
-      CK(launch_reduce(part + (size_t)nv * kRedBlocks, nblk, 1, dn, nullptr, nullptr, s));
-      CK(launch_reorth_flag(dh + nv, dn, 0.5, flag, s));
-      CK(Krylov<T>::dots(V, n, nv, w, n, part, false, flag, s));
-      CK(launch_reduce(part, nblk, nv, dh2, dh, flag, s));  // dh += second-pass coefficients
-      CK(Krylov<T>::update(V, n, nv, dh2, w, n, part, flag, s));
-      CK(launch_reduce(part + (size_t)nv * kRedBlocks, nblk, 1, dn, nullptr, flag, s));
-      CK(Krylov<T>::scale(w, w, n, reinterpret_cast<const double*>(dn), 0.0, s));
+      const double sz = sizeof(C<T>), ng = (nv + kDotGroup - 1) / kDotGroup;
+      KL(IE_K_DOTS, sz * n * (nv + ng), Krylov<T>::dots(V, n, nv, w, n, part, true, nullptr, s));
+      KL(IE_K_KRYLOV_MISC, 16.0 * (nv + 1) * nblk, launch_reduce(part, nblk, nv + 1, dh, nullptr, nullptr, s));
+      KL(IE_K_UPDATE, sz * n * (nv + 2), Krylov<T>::update(V, n, nv, dh, w, n, part, nullptr, s));
+      KL(IE_K_KRYLOV_MISC, 16.0 * nblk, launch_reduce(part + (size_t)nv * kRedBlocks, nblk, 1, dn, nullptr, nullptr, s));
+      KL(IE_K_KRYLOV_MISC, 0, launch_reorth_flag(dh + nv, dn, 0.5, flag, s));
+      // second Gram-Schmidt pass: launched always, runs only when the flag is set (bytes added below)
+      KL(IE_K_DOTS, 0, Krylov<T>::dots(V, n, nv, w, n, part, false, flag, s));
+      KL(IE_K_KRYLOV_MISC, 0, launch_reduce(part, nblk, nv, dh2, dh, flag, s));  // dh += second-pass coefficients
+      KL(IE_K_UPDATE, 0, Krylov<T>::update(V, n, nv, dh2, w, n, part, flag, s));
+      KL(IE_K_KRYLOV_MISC, 0, launch_reduce(part + (size_t)nv * kRedBlocks, nblk, 1, dn, nullptr, flag, s));
+      KL(IE_K_KRYLOV_MISC, 2 * sz * n, Krylov<T>::scale(w, w, n, reinterpret_cast<const double*>(dn), 0.0, s));
       CK(cudaMemcpyAsync(c->hpin, dh, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(c->hpin + nv, dn, sizeof(double2), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      CK(cudaMemcpyAsync(c->hpin + nv + 1, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(sync(c));
+      int reorth = 0;
+      std::memcpy(&reorth, c->hpin + nv + 1, sizeof(int));
+      if (reorth) {
+        c->prof.bytes[IE_K_DOTS] += sz * n * (nv + ng);
+        c->prof.bytes[IE_K_UPDATE] += sz * n * (nv + 2);
+        c->prof.bytes[IE_K_KRYLOV_MISC] += 16.0 * (nv + 1) * nblk;
+        out->reorth++;
+      }
       for (int i = 0; i < nv; ++i) Hij(i, j) = std::complex<double>(c->hpin[i].x, c->hpin[i].y);
       const double hn = std::sqrt(std::max(c->hpin[nv].x, 0.0));
       Hij(j + 1, j) = hn;
@@ -385,10 +471,10 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
     }
     for (int i = 0; i < jd; ++i) c->hpin[i] = make_double2(y[i].real(), y[i].imag());
     CK(cudaMemcpyAsync(c->dy.as<double2>(), c->hpin, sizeof(double2) * jd, cudaMemcpyHostToDevice, s));
-    CK(Krylov<T>::combine(V, n, jd, c->dy.as<double2>(), x, n, s));
+    KL(IE_K_KRYLOV_MISC, sizeof(C<T>) * (double)n * (jd + 2), Krylov<T>::combine(V, n, jd, c->dy.as<double2>(), x, n, s));
     CKS(A.apply(x, tmp));
     out->matvecs++;
-    CK(Krylov<T>::rsub(b, tmp, n, part, s));
+    KL(IE_K_KRYLOV_MISC, 3.0 * sizeof(C<T>) * n, Krylov<T>::rsub(b, tmp, n, part, s));
     double2 h;
     CKS(reduce_to_host(c, part, nblk, 1, &h));
     beta = std::sqrt(std::max(h.x, 0.0));
@@ -398,7 +484,7 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
       return IE_OK;
     }
     if (out->iters >= max_it || beta == 0.0) return IE_OK;
-    CK(Krylov<T>::scale(tmp, V, n, nullptr, 1.0 / beta, s));
+    KL(IE_K_KRYLOV_MISC, 2.0 * sizeof(C<T>) * n, Krylov<T>::scale(tmp, V, n, nullptr, 1.0 / beta, s));
   }
 }
 
@@ -487,13 +573,13 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
         CKS(norm_c128(c, c->E0.as<double2>(), c->N, nullptr, 0, c->N, &bnorm));
       } else {
         if (std::is_same<T, float>::value) {
-          CK(launch_c128_to_c64(Ei, c->N, reinterpret_cast<float2*>(dx), nb, nb, s));
+          KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(Ei, c->N, reinterpret_cast<float2*>(dx), nb, nb, s));
           CKS(A.apply(dx, t2));
           CKS(norm_c128(c, Ri, c->N, reinterpret_cast<const float2*>(t2), nb, nb, &bnorm));
         } else {
-          CK(launch_copy_c128(Ei, c->N, reinterpret_cast<double2*>(dx), nb, nb, s));
+          KL(IE_K_FIELD, 96.0 * nb, launch_copy_c128(Ei, c->N, reinterpret_cast<double2*>(dx), nb, nb, s));
           CKS(A.apply(dx, t2));
-          CK(launch_add_c128(Ri, c->N, reinterpret_cast<double2*>(t2), nb, nb, s));
+          KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(Ri, c->N, reinterpret_cast<double2*>(t2), nb, nb, s));
           CKS(norm_c128(c, reinterpret_cast<const double2*>(t2), nb, nullptr, 0, nb, &bnorm));
         }
       }
@@ -502,9 +588,9 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
       if (std::is_same<T, float>::value) tol_i = std::max(tol_i, cfg.dd_mode == IE_DD_NONE ? 1e-5 : 1e-6);
       tol_i = std::min(tol_i, 0.5);
       if (std::is_same<T, float>::value)
-        CK(launch_c128_to_c64(Ri, c->N, reinterpret_cast<float2*>(rhs), nb, nb, s));
+        KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(Ri, c->N, reinterpret_cast<float2*>(rhs), nb, nb, s));
       else
-        CK(launch_copy_c128(Ri, c->N, reinterpret_cast<double2*>(rhs), nb, nb, s));
+        KL(IE_K_FIELD, 96.0 * nb, launch_copy_c128(Ri, c->N, reinterpret_cast<double2*>(rhs), nb, nb, s));
       GmresOut go;
       CKS(gmres<T>(c, A, rhs, dx, true, tol_i, cfg.restart, cfg.max_inner, &go));
       inner_ok = inner_ok && go.converged;
@@ -512,9 +598,9 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
       info->gmres_iters_total += go.iters;
       info->matvecs += go.matvecs;
       if (std::is_same<T, float>::value)
-        CK(launch_add_c64_to_c128(reinterpret_cast<const float2*>(dx), nb, Ei, c->N, nb, s));
+        KL(IE_K_FIELD, 120.0 * nb, launch_add_c64_to_c128(reinterpret_cast<const float2*>(dx), nb, Ei, c->N, nb, s));
       else
-        CK(launch_add_c128(reinterpret_cast<const double2*>(dx), nb, Ei, c->N, nb, s));
+        KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(reinterpret_cast<const double2*>(dx), nb, Ei, c->N, nb, s));
       if (cfg.dd_mode == IE_DD_GAUSS_SEIDEL) {
         for (int j = i + 1; j < M; ++j) {  // interaction update of the later blocks (eq. 21)
           const BlockOp<T>& Bj = ops[j];
@@ -560,10 +646,10 @@ ie_status gmres_host(ie_ctx* c, int z0, int nz, const double* b, const double* x
     CK(bs.ensure(sizeof(float2) * n));
     CK(xs.ensure(sizeof(float2) * n));
     const long nb = A.nb();
-    CK(launch_c128_to_c64(bd.as<double2>(), nb, bs.as<float2>(), nb, nb, c->stream));
+    KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(bd.as<double2>(), nb, bs.as<float2>(), nb, nb, c->stream));
     bb = bs.as<C<T>>();
     xx = xs.as<C<T>>();
-    if (x0) CK(launch_c128_to_c64(xd.as<double2>(), nb, xs.as<float2>(), nb, nb, c->stream));
+    if (x0) KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(xd.as<double2>(), nb, xs.as<float2>(), nb, nb, c->stream));
   } else {
     bb = bd.as<C<T>>();
     xx = xd.as<C<T>>();
@@ -572,10 +658,10 @@ ie_status gmres_host(ie_ctx* c, int z0, int nz, const double* b, const double* x
   CKS(gmres<T>(c, A, bb, xx, x0 == nullptr, tol, restart, max_iter, &go));
   if (std::is_same<T, float>::value) {
     CK(cudaMemsetAsync(xd.p, 0, sizeof(double2) * n, c->stream));
-    CK(launch_add_c64_to_c128(xs.as<float2>(), A.nb(), xd.as<double2>(), A.nb(), A.nb(), c->stream));
+    KL(IE_K_FIELD, 120.0 * A.nb(), launch_add_c64_to_c128(xs.as<float2>(), A.nb(), xd.as<double2>(), A.nb(), A.nb(), c->stream));
   }
   CK(cudaMemcpyAsync(x, xd.p, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(sync(c));
   if (iters) *iters = go.iters;
   if (rel) *rel = go.rel;
   return go.converged ? IE_OK : IE_ENOCONV;
@@ -667,10 +753,11 @@ static ie_status set_contrast_dev_impl(ie_ctx* c, const double* s6_dev) {
   CKS(ensure_scalars(c));
   int* flag = c->flag.as<int>();
   CK(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
-  CK(launch_set_contrast(s6_dev, c->N, c->sigma0, c->ds64.as<double>(), c->ds32.as<float>(), flag, c->stream));
+  KL(IE_K_FIELD, 120.0 * c->N,
+     launch_set_contrast(s6_dev, c->N, c->sigma0, c->ds64.as<double>(), c->ds32.as<float>(), flag, c->stream));
   int bad = 0;
   CK(cudaMemcpyAsync(&c->hpin[0], flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(sync(c));
   std::memcpy(&bad, &c->hpin[0], sizeof(int));
   if (bad) {
     c->has_contrast = false;
@@ -740,7 +827,8 @@ ie_status ie_solve(ie_ctx* c, int32_t n_src, const ie_dipole* src, int32_t n_rx,
   }
   ie_status worst = IE_OK;
   for (int q = 0; q < n_src; ++q) {
-    CK(launch_incident_E(c->E0.as<double2>(), c->nx, c->ny, c->nz, c->origin, c->h, src[q].pos, src[q].moment, c->k0,
+    KL(IE_K_FIELD, 48.0 * c->N,
+       launch_incident_E(c->E0.as<double2>(), c->nx, c->ny, c->nz, c->origin, c->h, src[q].pos, src[q].moment, c->k0,
                          c->omega * kMu0, c->stream));
     ie_status st = cfg.precision == IE_PREC_FP64 ? solve_one<double>(c, cfg, &loc, q == 0)
                                                  : solve_one<float>(c, cfg, &loc, q == 0);
@@ -749,7 +837,8 @@ ie_status ie_solve(ie_ctx* c, int32_t n_src, const ie_dipole* src, int32_t n_rx,
     c->has_field = true;
     for (int r0 = 0; r0 < n_rx; r0 += kMaxRx) {
       const int nr = std::min(kMaxRx, n_rx - r0);
-      CK(launch_receivers(c->E.as<double2>(), c->N, c->ds64.as<double>(), c->N, c->nx, c->ny, c->origin, c->h,
+      KL(IE_K_FIELD, 96.0 * c->N,
+         launch_receivers(c->E.as<double2>(), c->N, c->ds64.as<double>(), c->N, c->nx, c->ny, c->origin, c->h,
                           c->rxdev.as<double>() + 3 * r0, nr, c->k0, c->rxpart.as<double2>(), src[q].pos,
                           src[q].moment, c->Hdev.as<double2>() + 3 * r0, c->stream));
     }
@@ -758,7 +847,7 @@ ie_status ie_solve(ie_ctx* c, int32_t n_src, const ie_dipole* src, int32_t n_rx,
                          c->stream));
     }
   }
-  CK(cudaStreamSynchronize(c->stream));
+  CK(sync(c));
   loc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = loc;
   if (worst == IE_ENOCONV) c->err = "tolerance not reached within the iteration limits";
@@ -769,7 +858,7 @@ ie_status ie_get_field(ie_ctx* c, double* E_out) {
   if (!c || !E_out) return fail(c, IE_EINVAL, "null argument");
   if (!c->has_field) return fail(c, IE_ESTATE, "no solve has run");
   CK(cudaMemcpyAsync(E_out, c->E.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(sync(c));
   return IE_OK;
 }
 
@@ -790,13 +879,13 @@ ie_status ie_matvec(ie_ctx* c, int32_t precision, int32_t z0, int32_t nz, const 
     CK(xs.ensure(sizeof(float2) * 3 * nb));
     CK(ys.ensure(sizeof(float2) * 3 * nb));
     CK(yd.ensure(sizeof(double2) * 3 * nb));
-    CK(launch_c128_to_c64(xd.as<double2>(), nb, xs.as<float2>(), nb, nb, c->stream));
+    KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(xd.as<double2>(), nb, xs.as<float2>(), nb, nb, c->stream));
     CKS(A.apply(xs.as<float2>(), ys.as<float2>()));
     CK(cudaMemsetAsync(yd.p, 0, sizeof(double2) * 3 * nb, c->stream));
-    CK(launch_add_c64_to_c128(ys.as<float2>(), nb, yd.as<double2>(), nb, nb, c->stream));
+    KL(IE_K_FIELD, 120.0 * nb, launch_add_c64_to_c128(ys.as<float2>(), nb, yd.as<double2>(), nb, nb, c->stream));
     CK(cudaMemcpyAsync(y, yd.p, sizeof(double2) * 3 * nb, cudaMemcpyDeviceToHost, c->stream));
   }
-  CK(cudaStreamSynchronize(c->stream));
+  CK(sync(c));
   return IE_OK;
 }
 
@@ -821,7 +910,7 @@ ie_status ie_interaction(ie_ctx* c, int32_t zs0, int32_t nzs, int32_t zt0, int32
   CKS(conv<double>(c, S, xd.as<double2>(), ns, zs0, nzs, zs0, nzt, zt0, EPI_CONV, nullptr, 0, yd.as<double2>(), nt,
                    nullptr, 0, nullptr, 0));
   CK(cudaMemcpyAsync(y, yd.p, sizeof(double2) * 3 * nt, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(sync(c));
   return IE_OK;
 }
 
@@ -838,7 +927,7 @@ ie_status ie_green_spectrum(ie_ctx* c, int32_t nz_set, int32_t comp, double* out
   CKS(get_spec(c, nz_set, &S));
   const long ocs = (long)(c->Lx / 2 + 1) * (c->Ly / 2 + 1) * (S->Lz / 2 + 1);
   CK(cudaMemcpyAsync(out, S->G64.as<double2>() + comp * ocs, sizeof(double2) * ocs, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(sync(c));
   if (dims) {
     dims[0] = c->Lx;
     dims[1] = c->Ly;
@@ -852,10 +941,11 @@ ie_status ie_incident_field(ie_ctx* c, const ie_dipole* src, double* E0_out) {
   CKS(check_point(c, src->pos));
   DevBuf e;
   CK(e.ensure(sizeof(double2) * 3 * c->N));
-  CK(launch_incident_E(e.as<double2>(), c->nx, c->ny, c->nz, c->origin, c->h, src->pos, src->moment, c->k0,
+  KL(IE_K_FIELD, 48.0 * c->N,
+     launch_incident_E(e.as<double2>(), c->nx, c->ny, c->nz, c->origin, c->h, src->pos, src->moment, c->k0,
                        c->omega * kMu0, c->stream));
   CK(cudaMemcpyAsync(E0_out, e.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(sync(c));
   return IE_OK;
 }
 
@@ -873,12 +963,13 @@ ie_status ie_receiver_fields(ie_ctx* c, const double* E, const ie_dipole* src, i
   CK(cudaMemcpyAsync(rxd.p, rx, sizeof(double) * 3 * n_rx, cudaMemcpyHostToDevice, c->stream));
   for (int r0 = 0; r0 < n_rx; r0 += kMaxRx) {
     const int nr = std::min(kMaxRx, n_rx - r0);
-    CK(launch_receivers(ed.as<double2>(), c->N, c->ds64.as<double>(), c->N, c->nx, c->ny, c->origin, c->h,
+    KL(IE_K_FIELD, 96.0 * c->N,
+       launch_receivers(ed.as<double2>(), c->N, c->ds64.as<double>(), c->N, c->nx, c->ny, c->origin, c->h,
                         rxd.as<double>() + 3 * r0, nr, c->k0, pd.as<double2>(), src->pos, src->moment,
                         hd.as<double2>() + 3 * r0, c->stream));
   }
   CK(cudaMemcpyAsync(H_out, hd.p, sizeof(double2) * 3 * n_rx, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(sync(c));
   return IE_OK;
 }
 
@@ -887,6 +978,29 @@ ie_status ie_fft_dims(const ie_ctx* c, int32_t nz_set, int32_t* dims) {
   dims[0] = c->Lx;
   dims[1] = c->Ly;
   dims[2] = next_pow2(2 * nz_set);
+  return IE_OK;
+}
+
+ie_status ie_profile_enable(ie_ctx* c, int32_t on) {
+  if (!c) return IE_EINVAL;
+  CK(sync(c));
+  auto& P = c->prof;
+  P.on = on != 0;
+  for (int k = 0; k < IE_K_COUNT; ++k) {
+    P.launches[k] = 0;
+    P.ms[k] = 0.0;
+    P.bytes[k] = 0.0;
+  }
+  return IE_OK;
+}
+
+ie_status ie_profile_read(const ie_ctx* cc, int32_t kclass, int64_t* launches, double* ms, double* bytes) {
+  if (!cc || kclass < 0 || kclass >= IE_K_COUNT) return IE_EINVAL;
+  ie_ctx* c = const_cast<ie_ctx*>(cc);  // folding finished events into the counters is not observable state
+  CK(drain(c));
+  if (launches) *launches = c->prof.launches[kclass];
+  if (ms) *ms = c->prof.ms[kclass];
+  if (bytes) *bytes = c->prof.bytes[kclass];
   return IE_OK;
 }
 

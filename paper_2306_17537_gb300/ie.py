@@ -21,6 +21,8 @@ IE_OK, IE_EINVAL, IE_ENOMEM, IE_ECUDA, IE_ENOCONV, IE_ESTATE = range(6)
 IE_DD_NONE, IE_DD_JACOBI, IE_DD_GAUSS_SEIDEL = range(3)
 IE_PREC_MIXED, IE_PREC_FP64 = range(2)
 IE_MAX_HISTORY = 128
+KERNEL_CLASSES = ("P1_c64", "P2_c64", "P3_c64", "P4_c64", "P5_c64", "P1_c128", "P2_c128", "P3_c128", "P4_c128",
+                  "P5_c128", "dots", "update", "krylov_misc", "field", "setup")
 STATUS_NAMES = {0: "IE_OK", 1: "IE_EINVAL", 2: "IE_ENOMEM", 3: "IE_ECUDA", 4: "IE_ENOCONV", 5: "IE_ESTATE"}
 
 
@@ -72,6 +74,8 @@ _SIGS = {
     "ie_incident_field": (ct.c_int, [_P, ct.POINTER(ie_dipole), _D]),
     "ie_receiver_fields": (ct.c_int, [_P, _D, ct.POINTER(ie_dipole), ct.c_int32, _D, _D]),
     "ie_fft_dims": (ct.c_int, [_P, ct.c_int32, ct.POINTER(ct.c_int32)]),
+    "ie_profile_enable": (ct.c_int, [_P, ct.c_int32]),
+    "ie_profile_read": (ct.c_int, [_P, ct.c_int32, ct.POINTER(ct.c_int64), _D, _D]),
     "ie_last_error": (ct.c_char_p, [_P]),
     "ie_destroy": (None, [_P]),
 }
@@ -238,6 +242,20 @@ class Context:
         d = _dipole(src)
         self._check(_lib.ie_receiver_fields(self.ptr, _dptr(EE), ct.byref(d), len(rx), _dptr(rx), _dptr(H)))
         return H
+
+    def profile_enable(self, on=True):
+        self._check(_lib.ie_profile_enable(self.ptr, int(bool(on))))
+
+    def profile_read(self):
+        """{class name: (launches, device ms, algorithmic bytes)} since the last profile_enable."""
+        out = {}
+        for k, name in enumerate(KERNEL_CLASSES):
+            n = ct.c_int64(0)
+            ms = ct.c_double(0.0)
+            by = ct.c_double(0.0)
+            self._check(_lib.ie_profile_read(self.ptr, k, ct.byref(n), ct.byref(ms), ct.byref(by)))
+            out[name] = (n.value, ms.value, by.value)
+        return out
 
     def fft_dims(self, nz_set=None):
         dims = (ct.c_int32 * 3)()
