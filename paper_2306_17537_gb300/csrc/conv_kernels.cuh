@@ -56,12 +56,12 @@ __global__ void __launch_bounds__(kThreads) k_p1_contrast_fftx(
     }
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) pencil_fft<T, L, -1>(J[c], t, sm, tw);
-  if (act) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < 3; ++c) {
+    pencil_fft<T, L, -1>(J[c], t, sm, tw);
+    if (act) {
 #pragma unroll
       for (int m = 0; m < E; ++m) A[c * A_cs + row * L + t + TT * m] = J[c][m];
+    }
   }
 }
 
@@ -136,34 +136,48 @@ __global__ void __launch_bounds__(kThreads) k_lanes_fft(
 // B holds planes of Ly*Lx; the source occupies pencil positions [os, os + nzs), the target is read
 // back from [ot, ot + nzt). With os = ot = 0 this is a block's own convolution; with the whole-domain
 // spectra and os/ot the blocks' z offsets it is the interaction between two sub-domains.
+// The three forward spectra are kept in shared memory (one buffer per component, also used for that
+// component's FFT exchanges), so a thread holds one pencil in registers at a time: 128-thread blocks
+// with 48 KB of shared memory, four blocks per SM.
+template <typename T, int L> struct P3Cfg {
+  static constexpr int TT = Plan<T, L>::TT;
+  static constexpr int W0 = 128 / TT;
+  static constexpr int W = W0 < 1 ? 1 : (W0 > 32 ? 32 : W0);
+};
+
 template <typename T, int L>
-__global__ void __launch_bounds__(kThreads) k_p3_spectral(
+__global__ void __launch_bounds__(128, 4) k_p3_spectral(
     const C<T>* __restrict__ Bin, long in_cs, int nzs, int os, C<T>* __restrict__ Bout, long out_cs,
     int nzt, int ot, const C<T>* __restrict__ G, int Lx, int Ly, const C<T>* __restrict__ tw) {
-  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = LaneCfg<T, L>::W;
-  __shared__ C<T> smem[L * W];
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = P3Cfg<T, L>::W;
+  __shared__ C<T> spec[3][L * W];
   const int w = threadIdx.x, t = threadIdx.y;
   const int kx = blockIdx.x * W + w, ky = blockIdx.y;
   const bool act = kx < Lx;
-  LaneSM<T, W> sm{smem + w};
   const long plane = (long)Ly * Lx, off = (long)ky * Lx + kx;
-  C<T> v[3][E];
+  C<T> v[E];
+  // forward z-FFT of each component; spectrum left in spec[c] at the thread's own positions
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    LaneSM<T, W> sm{spec[c] + w};
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int z = t + TT * m - os;
-    const bool ok = act && z >= 0 && z < nzs;
+    for (int m = 0; m < E; ++m) {
+      const int z = t + TT * m - os;
+      v[m] = (act && z >= 0 && z < nzs) ? Bin[c * in_cs + z * plane + off] : czero<C<T>>();
+    }
+    pencil_fft<T, L, -1>(v, t, sm, tw);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) v[c][m] = ok ? Bin[c * in_cs + z * plane + off] : czero<C<T>>();
+    for (int m = 0; m < E; ++m) sm.st(t + TT * m, v[m]);
   }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) pencil_fft<T, L, -1>(v[c], t, sm, tw);
+  // Green product at the thread's own frequencies (no other thread touches these slots)
   {
     const int ox = Lx / 2 + 1, oy = Ly / 2 + 1, oz = L / 2 + 1;
     const long ocs = (long)oz * oy * ox;
     const bool xlo = kx <= Lx / 2, ylo = ky <= Ly / 2;
     const int ix = xlo ? kx : Lx - kx, iy = ylo ? ky : Ly - ky;
     const T sxy = (xlo == ylo) ? (T)1 : (T)-1;
-#pragma unroll
+    LaneSM<T, W> s0{spec[0] + w}, s1{spec[1] + w}, s2{spec[2] + w};
+#pragma unroll 4
     for (int m = 0; m < E; ++m) {
       const int kz = t + TT * m;
       const bool zlo = kz <= L / 2;
@@ -173,22 +187,27 @@ __global__ void __launch_bounds__(kThreads) k_p3_spectral(
         const C<T>* g = G + ((long)iz * oy + iy) * ox + ix;
         const C<T> gxx = __ldg(g), gyy = __ldg(g + ocs), gzz = __ldg(g + 2 * ocs);
         const C<T> gxy = sxy * __ldg(g + 3 * ocs), gxz = sxz * __ldg(g + 4 * ocs), gyz = syz * __ldg(g + 5 * ocs);
-        const C<T> j0 = v[0][m], j1 = v[1][m], j2 = v[2][m];
-        v[0][m] = cmul(gxx, j0) + cmul(gxy, j1) + cmul(gxz, j2);
-        v[1][m] = cmul(gxy, j0) + cmul(gyy, j1) + cmul(gyz, j2);
-        v[2][m] = cmul(gxz, j0) + cmul(gyz, j1) + cmul(gzz, j2);
+        const C<T> j0 = s0.ld(kz), j1 = s1.ld(kz), j2 = s2.ld(kz);
+        s0.st(kz, cmul(gxx, j0) + cmul(gxy, j1) + cmul(gxz, j2));
+        s1.st(kz, cmul(gxy, j0) + cmul(gyy, j1) + cmul(gyz, j2));
+        s2.st(kz, cmul(gxz, j0) + cmul(gyz, j1) + cmul(gzz, j2));
       }
     }
   }
+  // inverse z-FFT of each component and crop
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    LaneSM<T, W> sm{spec[c] + w};
 #pragma unroll
-  for (int c = 0; c < 3; ++c) pencil_fft<T, L, +1>(v[c], t, sm, tw);
-  if (!act) return;
+    for (int m = 0; m < E; ++m) v[m] = sm.ld(t + TT * m);
+    __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]
+    pencil_fft<T, L, +1>(v, t, sm, tw);
+    if (act) {
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int z = t + TT * m - ot;
-    if (z >= 0 && z < nzt) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Bout[c * out_cs + z * plane + off] = v[c][m];
+      for (int m = 0; m < E; ++m) {
+        const int z = t + TT * m - ot;
+        if (z >= 0 && z < nzt) Bout[c * out_cs + z * plane + off] = v[m];
+      }
     }
   }
 }

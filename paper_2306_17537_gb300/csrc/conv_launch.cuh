@@ -113,7 +113,7 @@ cudaError_t ConvLaunch<T>::p3(int L, const C<T>* Bin, long in_cs, int nzs, int o
   switch (L) {
 #define IE_CASE(N)                                                                                            \
   case N: {                                                                                                   \
-    constexpr int W = LaneCfg<T, N>::W;                                                                       \
+    constexpr int W = P3Cfg<T, N>::W;                                                                         \
     dim3 blk(W, Plan<T, N>::TT), grd((unsigned)((Lx + W - 1) / W), (unsigned)Ly);                            \
     k_p3_spectral<T, N><<<grd, blk, 0, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw);       \
     break;                                                                                                    \

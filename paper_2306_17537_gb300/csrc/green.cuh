@@ -21,42 +21,46 @@ cudaError_t launch_receivers(const double2* E, long e_cs, const double* ds, long
                              const double* m, double2* H, cudaStream_t s);
 
 // ------------------------------------------------------------------ Krylov vector operations
-// Vectors are n complex entries (float2 or double2); a basis is nv vectors at stride ld.
-constexpr int kDotGroup = 8;    // basis vectors per dot-product block row
-constexpr int kRedBlocks = 608;  // upper bound on partial-sum blocks (4 per SM)
+// Vectors are n complex entries (float2 or double2), 16-byte aligned; a basis is nv vectors at
+// stride ld (ld even). Every reduction finishes inside its kernel (last block) and writes FP64
+// results to device memory; RedScratch holds the per-block partials and the arrival counters
+// (zero-initialised once, reset by the kernels).
+constexpr int kDotGroup = 8;     // basis vectors per dot-product block row
+constexpr int kRedBlocks = 608;  // upper bound on reduction blocks (4 per SM)
+constexpr int kRedSlots = 136;   // partial-sum rows (basis up to 127 vectors + norm)
+constexpr int kCounterUpdate = 16, kCounterNorm = 17, kCounters = 32;
+struct RedScratch {
+  double2* part;       // [kRedSlots][kRedBlocks]
+  unsigned* counters;  // [kCounters], zero
+};
 
 template <typename T> struct Krylov {
-  // part[k * kRedBlocks + b] = sum over block b of conj(V_k) w   (k < nv);  part[nv*kRedBlocks + b] = |w|^2
-  static cudaError_t dots(const C<T>* V, long ld, int nv, const C<T>* w, long n, double2* part, bool with_norm,
-                          const int* skip, cudaStream_t s);
-  // w -= sum_k h_k V_k; optional |w|^2 partials into part (as .x)
-  static cudaError_t update(const C<T>* V, long ld, int nv, const double2* h, C<T>* w, long n, double2* part,
-                            const int* skip, cudaStream_t s);
+  // out[k] = V_k^H w (k < nv) and, with_norm, out[nv] = |w|^2; acc[k] += out[k] when acc != null.
+  // Does nothing when skip != null and *skip == 0.
+  static cudaError_t dots(const C<T>* V, long ld, int nv, const C<T>* w, long n, bool with_norm, double2* out,
+                          double2* acc, const int* skip, const RedScratch& sc, cudaStream_t s);
+  // w -= sum_k h_k V_k, *out_norm = |w|^2; with flag: *flag = (|w|^2 < eta2 * ref->x). skip as above.
+  static cudaError_t update(const C<T>* V, long ld, int nv, const double2* h, C<T>* w, long n, double2* out_norm,
+                            const double2* ref, double eta2, int* flag, const int* skip, const RedScratch& sc,
+                            cudaStream_t s);
   // x += sum_k y_k V_k
   static cudaError_t combine(const C<T>* V, long ld, int nv, const double2* y, C<T>* x, long n, cudaStream_t s);
-  // dst = src * scale, scale = 1/sqrt(*nrm2) (0 if *nrm2 == 0) or a host value when nrm2 == nullptr
-  static cudaError_t scale(const C<T>* src, C<T>* dst, long n, const double* nrm2, double host_scale, cudaStream_t s);
-  // partial |v|^2
-  static cudaError_t norm2(const C<T>* v, long n, double2* part, cudaStream_t s);
-  // y = b - y  (used for the true residual b - A x with A x already in y); |y|^2 partials
-  static cudaError_t rsub(const C<T>* b, C<T>* y, long n, double2* part, cudaStream_t s);
+  // dst = src / sqrt(nrm2->x) (0 if the norm is 0), or dst = src * host_scale when nrm2 is null
+  static cudaError_t scale(const C<T>* src, C<T>* dst, long n, const double2* nrm2, double host_scale, cudaStream_t s);
+  // *out = |v|^2
+  static cudaError_t norm2(const C<T>* v, long n, double2* out, const RedScratch& sc, cudaStream_t s);
+  // y = b - y, *out = |y|^2  (true residual b - A x with A x already in y)
+  static cudaError_t rsub(const C<T>* b, C<T>* y, long n, double2* out, const RedScratch& sc, cudaStream_t s);
 };
 int krylov_blocks(long n);
-// out[k] = sum_b part[k*kRedBlocks + b] for k < nk (nblk partials per row); if out2, also out2[k] += out[k].
-// Skipped entirely when skip != nullptr and *skip == 0.
-cudaError_t launch_reduce(const double2* part, int nblk, int nk, double2* out, double2* out2, const int* skip,
-                          cudaStream_t s);
-// flag = (nrm2_after < eta^2 * nrm2_before): reorthogonalisation needed
-cudaError_t launch_reorth_flag(const double2* nrm_before, const double2* nrm_after, double eta2, int* flag,
-                               cudaStream_t s);
 
 // c128 <-> c64 helpers on strided 3-component fields (slab of a whole-domain field)
 cudaError_t launch_c128_to_c64(const double2* src, long src_cs, float2* dst, long dst_cs, long n, cudaStream_t s);
 cudaError_t launch_add_c64_to_c128(const float2* src, long src_cs, double2* dst, long dst_cs, long n, cudaStream_t s);
 cudaError_t launch_add_c128(const double2* src, long src_cs, double2* dst, long dst_cs, long n, cudaStream_t s);
 cudaError_t launch_copy_c128(const double2* src, long src_cs, double2* dst, long dst_cs, long n, cudaStream_t s);
-// partial sums of |a + b|^2 (b may be null) over a 3-component strided field (FP64 inputs or f32 b)
-cudaError_t launch_norm2_c128(const double2* a, long a_cs, const float2* b, long b_cs, long n, double2* part,
-                              cudaStream_t s);
+// *out = |a + b|^2 over a 3-component strided field (b optional, complex64)
+cudaError_t launch_norm2_c128(const double2* a, long a_cs, const float2* b, long b_cs, long n, double2* out,
+                              const RedScratch& sc, cudaStream_t s);
 
 }  // namespace ie

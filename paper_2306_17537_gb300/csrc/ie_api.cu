@@ -88,7 +88,7 @@ struct ie_ctx {
 
   // Krylov workspace (one precision at a time; sized on demand)
   DevBuf V, kx, kb, kt1, kt2;
-  DevBuf part, dh, dh2, dnrm, dy, flag, rxdev, Hdev, rxpart;
+  DevBuf part, counters, dh, dh2, dnrm, dy, flag, rxdev, Hdev, rxpart;
   double2* hpin = nullptr;  // pinned host scratch for small reductions
 
   struct Prof {  // launch accounting (ie_profile_enable / ie_profile_read)
@@ -312,7 +312,11 @@ template <typename T> ie_status make_block(ie_ctx* c, int z0, int nz, BlockOp<T>
 }
 
 ie_status ensure_scalars(ie_ctx* c) {
-  CK(c->part.ensure(sizeof(double2) * kRedBlocks * 160));
+  if (!c->counters.p) {
+    CK(c->counters.ensure(sizeof(unsigned) * kCounters));
+    CK(cudaMemsetAsync(c->counters.p, 0, sizeof(unsigned) * kCounters, c->stream));
+  }
+  CK(c->part.ensure(sizeof(double2) * kRedBlocks * kRedSlots));
   CK(c->dh.ensure(sizeof(double2) * 160));
   CK(c->dh2.ensure(sizeof(double2) * 160));
   CK(c->dnrm.ensure(sizeof(double2) * 8));
@@ -322,27 +326,30 @@ ie_status ensure_scalars(ie_ctx* c) {
   return IE_OK;
 }
 
-// FP64 sum of partials -> host
-ie_status reduce_to_host(ie_ctx* c, const double2* part, int nblk, int nk, double2* host) {
-  KL(IE_K_KRYLOV_MISC, 16.0 * nk * nblk, launch_reduce(part, nblk, nk, c->dh2.as<double2>(), nullptr, nullptr, c->stream));
-  CK(cudaMemcpyAsync(c->hpin, c->dh2.as<double2>(), sizeof(double2) * nk, cudaMemcpyDeviceToHost, c->stream));
+RedScratch scratch(ie_ctx* c) { return RedScratch{c->part.as<double2>(), c->counters.as<unsigned>()}; }
+
+// device FP64 scalar -> host
+ie_status scalar_to_host(ie_ctx* c, const double2* dev, double2* host) {
+  CK(cudaMemcpyAsync(c->hpin, dev, sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
   CK(sync(c));
-  std::memcpy(host, c->hpin, sizeof(double2) * nk);
+  *host = c->hpin[0];
   return IE_OK;
 }
 
 template <typename T> ie_status vnorm(ie_ctx* c, const C<T>* v, long n, double* out) {
-  KL(IE_K_KRYLOV_MISC, sizeof(C<T>) * (double)n, Krylov<T>::norm2(v, n, c->part.as<double2>(), c->stream));
+  double2* d = c->dnrm.as<double2>() + 2;
+  KL(IE_K_KRYLOV_MISC, sizeof(C<T>) * (double)n, Krylov<T>::norm2(v, n, d, scratch(c), c->stream));
   double2 h;
-  CKS(reduce_to_host(c, c->part.as<double2>(), krylov_blocks(n), 1, &h));
+  CKS(scalar_to_host(c, d, &h));
   *out = std::sqrt(std::max(h.x, 0.0));
   return IE_OK;
 }
 
 ie_status norm_c128(ie_ctx* c, const double2* a, long a_cs, const float2* b, long b_cs, long n, double* out) {
-  KL(IE_K_FIELD, (16.0 + (b ? 8.0 : 0.0)) * 3 * n, launch_norm2_c128(a, a_cs, b, b_cs, n, c->part.as<double2>(), c->stream));
+  double2* d = c->dnrm.as<double2>() + 3;
+  KL(IE_K_FIELD, (16.0 + (b ? 8.0 : 0.0)) * 3 * n, launch_norm2_c128(a, a_cs, b, b_cs, n, d, scratch(c), c->stream));
   double2 h;
-  CKS(reduce_to_host(c, c->part.as<double2>(), kRedBlocks, 1, &h));
+  CKS(scalar_to_host(c, d, &h));
   *out = std::sqrt(std::max(h.x, 0.0));
   return IE_OK;
 }
@@ -365,11 +372,12 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
   cudaStream_t s = c->stream;
   CKS(ensure_scalars(c));
   if (m < 1 || m > 127) return fail(c, IE_EINVAL, "restart must be in [1, 127]");
-  CK(c->V.ensure(sizeof(C<T>) * (size_t)(m + 1) * n));
+  const long ld = (n + 1) & ~1L;  // even stride keeps every basis vector 16-byte aligned
+  CK(c->V.ensure(sizeof(C<T>) * (size_t)(m + 1) * ld));
   CK(c->kt1.ensure(sizeof(C<T>) * (size_t)n));
   C<T>* V = c->V.as<C<T>>();
   C<T>* tmp = c->kt1.as<C<T>>();
-  double2* part = c->part.as<double2>();
+  const RedScratch sc = scratch(c);
   double2* dh = c->dh.as<double2>();
   double2* dh2 = c->dh2.as<double2>();
   double2* dn = c->dnrm.as<double2>();
@@ -391,9 +399,9 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
   } else {
     CKS(A.apply(x, tmp));
     out->matvecs++;
-    KL(IE_K_KRYLOV_MISC, 3.0 * sizeof(C<T>) * n, Krylov<T>::rsub(b, tmp, n, part, s));
+    KL(IE_K_KRYLOV_MISC, 3.0 * sizeof(C<T>) * n, Krylov<T>::rsub(b, tmp, n, dn + 1, sc, s));
     double2 h;
-    CKS(reduce_to_host(c, part, krylov_blocks(n), 1, &h));
+    CKS(scalar_to_host(c, dn + 1, &h));
     beta = std::sqrt(std::max(h.x, 0.0));
     if (beta / bnorm <= tol) {
       out->rel = beta / bnorm;
@@ -403,7 +411,6 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
     KL(IE_K_KRYLOV_MISC, 2.0 * sizeof(C<T>) * n, Krylov<T>::scale(tmp, V, n, nullptr, 1.0 / beta, s));
   }
   out->rel = beta / bnorm;
-  const int nblk = krylov_blocks(n);
   std::vector<std::complex<double>> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   auto Hij = [&](int i, int j) -> std::complex<double>& { return H[(size_t)i * m + j]; };
   while (true) {
@@ -413,22 +420,18 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
     int jd = 0;
     bool breakdown = false;
     for (int j = 0; j < m; ++j) {
-      C<T>* w = V + (size_t)(j + 1) * n;
-      CKS(A.apply(V + (size_t)j * n, w));
+      C<T>* w = V + (size_t)(j + 1) * ld;
+      CKS(A.apply(V + (size_t)j * ld, w));
       out->matvecs++;
       const int nv = j + 1;
       const double sz = sizeof(C<T>), ng = (nv + kDotGroup - 1) / kDotGroup;
-      KL(IE_K_DOTS, sz * n * (nv + ng), Krylov<T>::dots(V, n, nv, w, n, part, true, nullptr, s));
-      KL(IE_K_KRYLOV_MISC, 16.0 * (nv + 1) * nblk, launch_reduce(part, nblk, nv + 1, dh, nullptr, nullptr, s));
-      KL(IE_K_UPDATE, sz * n * (nv + 2), Krylov<T>::update(V, n, nv, dh, w, n, part, nullptr, s));
-      KL(IE_K_KRYLOV_MISC, 16.0 * nblk, launch_reduce(part + (size_t)nv * kRedBlocks, nblk, 1, dn, nullptr, nullptr, s));
-      KL(IE_K_KRYLOV_MISC, 0, launch_reorth_flag(dh + nv, dn, 0.5, flag, s));
-      // second Gram-Schmidt pass: launched always, runs only when the flag is set (bytes added below)
-      KL(IE_K_DOTS, 0, Krylov<T>::dots(V, n, nv, w, n, part, false, flag, s));
-      KL(IE_K_KRYLOV_MISC, 0, launch_reduce(part, nblk, nv, dh2, dh, flag, s));  // dh += second-pass coefficients
-      KL(IE_K_UPDATE, 0, Krylov<T>::update(V, n, nv, dh2, w, n, part, flag, s));
-      KL(IE_K_KRYLOV_MISC, 0, launch_reduce(part + (size_t)nv * kRedBlocks, nblk, 1, dn, nullptr, flag, s));
-      KL(IE_K_KRYLOV_MISC, 2 * sz * n, Krylov<T>::scale(w, w, n, reinterpret_cast<const double*>(dn), 0.0, s));
+      // first pass: dh[0..j] = V^H w, dh[nv] = |w|^2; w -= V dh, dn = |w|^2, flag = (|w| dropped below 1/sqrt 2)
+      KL(IE_K_DOTS, sz * n * (nv + ng), Krylov<T>::dots(V, ld, nv, w, n, true, dh, nullptr, nullptr, sc, s));
+      KL(IE_K_UPDATE, sz * n * (nv + 2), Krylov<T>::update(V, ld, nv, dh, w, n, dn, dh + nv, 0.5, flag, nullptr, sc, s));
+      // second pass, launched always but run only when the flag is set (its bytes are added below)
+      KL(IE_K_DOTS, 0, Krylov<T>::dots(V, ld, nv, w, n, false, dh2, dh, flag, sc, s));
+      KL(IE_K_UPDATE, 0, Krylov<T>::update(V, ld, nv, dh2, w, n, dn, nullptr, 0.0, nullptr, flag, sc, s));
+      KL(IE_K_KRYLOV_MISC, 2 * sz * n, Krylov<T>::scale(w, w, n, dn, 0.0, s));
       CK(cudaMemcpyAsync(c->hpin, dh, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(c->hpin + nv, dn, sizeof(double2), cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(c->hpin + nv + 1, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -438,7 +441,6 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
       if (reorth) {
         c->prof.bytes[IE_K_DOTS] += sz * n * (nv + ng);
         c->prof.bytes[IE_K_UPDATE] += sz * n * (nv + 2);
-        c->prof.bytes[IE_K_KRYLOV_MISC] += 16.0 * (nv + 1) * nblk;
         out->reorth++;
       }
       for (int i = 0; i < nv; ++i) Hij(i, j) = std::complex<double>(c->hpin[i].x, c->hpin[i].y);
@@ -471,12 +473,12 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
     }
     for (int i = 0; i < jd; ++i) c->hpin[i] = make_double2(y[i].real(), y[i].imag());
     CK(cudaMemcpyAsync(c->dy.as<double2>(), c->hpin, sizeof(double2) * jd, cudaMemcpyHostToDevice, s));
-    KL(IE_K_KRYLOV_MISC, sizeof(C<T>) * (double)n * (jd + 2), Krylov<T>::combine(V, n, jd, c->dy.as<double2>(), x, n, s));
+    KL(IE_K_KRYLOV_MISC, sizeof(C<T>) * (double)n * (jd + 2), Krylov<T>::combine(V, ld, jd, c->dy.as<double2>(), x, n, s));
     CKS(A.apply(x, tmp));
     out->matvecs++;
-    KL(IE_K_KRYLOV_MISC, 3.0 * sizeof(C<T>) * n, Krylov<T>::rsub(b, tmp, n, part, s));
+    KL(IE_K_KRYLOV_MISC, 3.0 * sizeof(C<T>) * n, Krylov<T>::rsub(b, tmp, n, dn + 1, sc, s));
     double2 h;
-    CKS(reduce_to_host(c, part, nblk, 1, &h));
+    CKS(scalar_to_host(c, dn + 1, &h));
     beta = std::sqrt(std::max(h.x, 0.0));
     out->rel = beta / bnorm;
     if (out->rel <= tol) {

@@ -1,24 +1,62 @@
-// Krylov vector kernels for GMRES (Arnoldi with classical Gram-Schmidt and selective
-// re-orthogonalisation). Vectors are complex64 (mixed precision) or complex128; every inner product
-// and norm is accumulated in FP64 across threads and blocks. In the complex64 case each thread first
-// sums kChunk consecutive products in FP32 before adding them into its FP64 accumulator, which keeps
-// the FP64 add rate (far below the FP32 rate on this part) off the critical path.
-#include <type_traits>
-
+// Krylov vector kernels for GMRES: Arnoldi by classical Gram-Schmidt with a second pass on demand,
+// basis combination, norms.
+//
+// Vectors are complex64 (mixed precision) or complex128, 16-byte aligned, read as 16-byte packets
+// (two complex64 or one complex128 values). Every inner product and norm is reduced in FP64 across
+// threads and blocks. Within a thread the complex64 products are summed in FP32 with Kahan
+// compensation, so the accumulated rounding stays at the level of the FP32 products themselves
+// while the FP64 pipe (a small fraction of the FP32 rate on this part) is only used once per thread.
+// Each reduction finishes in the last block to arrive (partials summed in a fixed order, so the
+// result is deterministic); no separate reduction launch is needed.
 #include "green.cuh"
 
 namespace ie {
 
 constexpr int kKThreads = 256;
-constexpr int kChunk = 8;
 constexpr int kMaxBasis = 128;
 
 int krylov_blocks(long n) {
-  long g = (n + (long)kKThreads * kChunk - 1) / ((long)kKThreads * kChunk);
+  long g = (n / 2 + kKThreads - 1) / kKThreads;
   if (g > kRedBlocks) g = kRedBlocks;
   if (g < 1) g = 1;
   return (int)g;
 }
+
+// ------------------------------------------------------------------ packets and accumulators
+template <typename T> struct Pk;
+template <> struct Pk<float> {
+  using P = float4;
+  static constexpr int CPP = 2;
+  __device__ __forceinline__ static float2 get(const P& p, int j) { return j ? make_float2(p.z, p.w) : make_float2(p.x, p.y); }
+  __device__ __forceinline__ static P make(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+};
+template <> struct Pk<double> {
+  using P = double2;
+  static constexpr int CPP = 1;
+  __device__ __forceinline__ static double2 get(const P& p, int) { return p; }
+  __device__ __forceinline__ static P make(double2 a, double2) { return a; }
+};
+
+template <typename T> struct Acc;  // per-thread complex accumulator
+template <> struct Acc<float> {    // Kahan-compensated FP32
+  float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+  __device__ __forceinline__ void add(float2 x) {
+    float yr = x.x - c.x, tr = s.x + yr;
+    c.x = (tr - s.x) - yr;
+    s.x = tr;
+    float yi = x.y - c.y, ti = s.y + yi;
+    c.y = (ti - s.y) - yi;
+    s.y = ti;
+  }
+  __device__ __forceinline__ double2 value() const {
+    return make_double2((double)s.x - (double)c.x, (double)s.y - (double)c.y);
+  }
+};
+template <> struct Acc<double> {
+  double2 s = make_double2(0.0, 0.0);
+  __device__ __forceinline__ void add(double2 x) { s = s + x; }
+  __device__ __forceinline__ double2 value() const { return s; }
+};
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
 #pragma unroll
@@ -29,118 +67,174 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
   return v;
 }
 
-// Block-reduce NQ double2 accumulators and write them to part[q * kRedBlocks + blockIdx.x].
-template <int NQ>
-__device__ __forceinline__ void block_store(double2 (&acc)[NQ], int nq, double2* part, int slot0) {
-  __shared__ double2 red[NQ][kKThreads / 32];
+// Sum one value per thread over the block (FP64); result valid in thread 0.
+__device__ __forceinline__ double2 block_sum(double2 v, double2* red /* [kKThreads/32] shared */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    double2 v = warp_sum(acc[q]);
-    if (lane == 0) red[q][warp] = v;
-  }
+  v = warp_sum(v);
   __syncthreads();
-  if (threadIdx.x < nq) {
-    double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int w = 0; w < kKThreads / 32; ++w) s = s + red[threadIdx.x][w];
-    part[(long)(slot0 + threadIdx.x) * kRedBlocks + blockIdx.x] = s;
-  }
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double2 s = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kKThreads / 32; ++w) s = s + red[w];
+  return s;
 }
 
+// Last-block detection after this block has written its partials.
+__device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned nblocks) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == nblocks - 1);
+  __syncthreads();
+  return last;
+}
+
+// Fixed-order sum of the partials of one slot by the whole block; result in thread 0.
+__device__ __forceinline__ double2 sum_partials(const double2* part, int nblk, double2* red) {
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = threadIdx.x; b < nblk; b += kKThreads) s = s + __ldcg(part + b);
+  return block_sum(s, red);
+}
+
+// ------------------------------------------------------------------ inner products V^H w (+ |w|^2)
 template <typename T>
 __global__ void __launch_bounds__(kKThreads) k_dots(const C<T>* __restrict__ V, long ld, int nv,
-                                                   const C<T>* __restrict__ w, long n, double2* __restrict__ part,
-                                                   int with_norm, const int* __restrict__ skip) {
+                                                   const C<T>* __restrict__ w, long n, int with_norm,
+                                                   double2* __restrict__ part, unsigned* __restrict__ counters,
+                                                   double2* __restrict__ out, double2* __restrict__ acc,
+                                                   const int* __restrict__ skip) {
   if (skip && *skip == 0) return;
-  const int k0 = blockIdx.y * kDotGroup;
-  const int nk = min(kDotGroup, nv - k0);
-  const bool do_norm = with_norm && blockIdx.y == 0;
-  double2 acc[kDotGroup + 1];
+  using K = Pk<T>;
+  constexpr int G = kDotGroup, CPP = K::CPP;
+  __shared__ double2 red[kKThreads / 32];
+  const int g = blockIdx.y, k0 = g * G, nk = min(G, nv - k0);
+  const bool dn = with_norm && g == 0;
+  Acc<T> a[G];
+  Acc<T> an;
+  const long np = n / CPP;
+  const typename K::P* wp = reinterpret_cast<const typename K::P*>(w);
+  for (long p = (long)blockIdx.x * kKThreads + threadIdx.x; p < np; p += (long)gridDim.x * kKThreads) {
+    const typename K::P wv = __ldcs(wp + p);
+    typename K::P vv[G];
 #pragma unroll
-  for (int q = 0; q <= kDotGroup; ++q) acc[q] = make_double2(0.0, 0.0);
-  const long step = (long)gridDim.x * kKThreads * kChunk;
-  for (long base = (long)blockIdx.x * kKThreads * kChunk; base < n; base += step) {
-    C<T> a[kDotGroup + 1];
+    for (int q = 0; q < G; ++q)
+      if (q < nk) vv[q] = __ldcs(reinterpret_cast<const typename K::P*>(V + (long)(k0 + q) * ld) + p);
 #pragma unroll
-    for (int q = 0; q <= kDotGroup; ++q) a[q] = czero<C<T>>();
+    for (int q = 0; q < G; ++q)
+      if (q < nk) {
+        C<T> t = czero<C<T>>();
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) {
-      const long e = base + i * kKThreads + threadIdx.x;
-      if (e < n) {
-        const C<T> we = w[e];
-#pragma unroll
-        for (int q = 0; q < kDotGroup; ++q)
-          if (q < nk) {
-            const C<T> v = V[(long)(k0 + q) * ld + e];
-            a[q].x += v.x * we.x + v.y * we.y;
-            a[q].y += v.x * we.y - v.y * we.x;
-          }
-        if (do_norm) a[kDotGroup].x += we.x * we.x + we.y * we.y;
+        for (int j = 0; j < CPP; ++j) {
+          const C<T> v = K::get(vv[q], j), x = K::get(wv, j);
+          t.x += v.x * x.x + v.y * x.y;
+          t.y += v.x * x.y - v.y * x.x;
+        }
+        a[q].add(t);
       }
-    }
+    if (dn) {
+      T s = 0;
 #pragma unroll
-    for (int q = 0; q <= kDotGroup; ++q) acc[q] = acc[q] + to_c64(a[q]);
-  }
-  // slots k0..k0+nk-1 hold the dots; the norm goes to slot nv (written by group 0 only)
-  double2 out[kDotGroup + 1];
-#pragma unroll
-  for (int q = 0; q < kDotGroup; ++q) out[q] = acc[q];
-  out[kDotGroup] = acc[kDotGroup];
-  __shared__ double2 red[kDotGroup + 1][kKThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q <= kDotGroup; ++q) {
-    double2 v = warp_sum(out[q]);
-    if (lane == 0) red[q][warp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x <= kDotGroup) {
-    const int q = threadIdx.x;
-    const bool isnorm = (q == kDotGroup);
-    if ((isnorm && do_norm) || (!isnorm && q < nk)) {
-      double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int w2 = 0; w2 < kKThreads / 32; ++w2) s = s + red[q][w2];
-      const int slot = isnorm ? nv : k0 + q;
-      part[(long)slot * kRedBlocks + blockIdx.x] = s;
+      for (int j = 0; j < CPP; ++j) {
+        const C<T> x = K::get(wv, j);
+        s += x.x * x.x + x.y * x.y;
+      }
+      an.add(mk<T>(s, 0));
     }
   }
+  if (CPP == 2 && (n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // odd tail element
+    const C<T> x = w[n - 1];
+    for (int q = 0; q < nk; ++q) {
+      const C<T> v = V[(long)(k0 + q) * ld + n - 1];
+      a[q].add(mk<T>(v.x * x.x + v.y * x.y, v.x * x.y - v.y * x.x));
+    }
+    if (dn) an.add(mk<T>(x.x * x.x + x.y * x.y, 0));
+  }
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    if (q < nk) {
+      const double2 s = block_sum(a[q].value(), red);
+      if (threadIdx.x == 0) part[(long)(k0 + q) * kRedBlocks + blockIdx.x] = s;
+    }
+  }
+  if (dn) {
+    const double2 s = block_sum(an.value(), red);
+    if (threadIdx.x == 0) part[(long)nv * kRedBlocks + blockIdx.x] = s;
+  }
+  if (!arrive_last(counters + g, gridDim.x)) return;
+  for (int q = 0; q <= nk; ++q) {
+    const int slot = (q < nk) ? k0 + q : nv;
+    if (q == nk && !dn) break;
+    const double2 s = sum_partials(part + (long)slot * kRedBlocks, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      out[slot] = s;
+      if (acc && slot < nv) acc[slot] = acc[slot] + s;
+    }
+  }
+  if (threadIdx.x == 0) counters[g] = 0u;
 }
 
+// ------------------------------------------------------------------ w -= sum_k h_k V_k ; |w|^2
 template <typename T>
 __global__ void __launch_bounds__(kKThreads) k_update(const C<T>* __restrict__ V, long ld, int nv,
                                                      const double2* __restrict__ h, C<T>* __restrict__ w, long n,
-                                                     double2* __restrict__ part, const int* __restrict__ skip) {
+                                                     double2* __restrict__ part, unsigned* __restrict__ counter,
+                                                     double2* __restrict__ out_norm, const double2* __restrict__ ref,
+                                                     double eta2, int* __restrict__ flag, const int* __restrict__ skip) {
   if (skip && *skip == 0) return;
+  using K = Pk<T>;
+  constexpr int CPP = K::CPP;
   __shared__ C<T> hs[kMaxBasis];
+  __shared__ double2 red[kKThreads / 32];
   for (int k = threadIdx.x; k < nv; k += kKThreads) hs[k] = to_c(h[k], T());
   __syncthreads();
-  double2 acc[1] = {make_double2(0.0, 0.0)};
-  const long step = (long)gridDim.x * kKThreads * kChunk;
-  for (long base = (long)blockIdx.x * kKThreads * kChunk; base < n; base += step) {
-    T a = 0;
+  Acc<T> an;
+  const long np = n / CPP;
+  typename K::P* wp = reinterpret_cast<typename K::P*>(w);
+  for (long p = (long)blockIdx.x * kKThreads + threadIdx.x; p < np; p += (long)gridDim.x * kKThreads) {
+    const typename K::P wv = wp[p];
+    C<T> r[CPP];
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) {
-      const long e = base + i * kKThreads + threadIdx.x;
-      if (e < n) {
-        C<T> r = w[e];
-        int k = 0;
-        for (; k + 4 <= nv; k += 4) {
-          const C<T> v0 = V[(long)k * ld + e], v1 = V[(long)(k + 1) * ld + e];
-          const C<T> v2 = V[(long)(k + 2) * ld + e], v3 = V[(long)(k + 3) * ld + e];
-          r = r - cmul(hs[k], v0) - cmul(hs[k + 1], v1) - cmul(hs[k + 2], v2) - cmul(hs[k + 3], v3);
-        }
-        for (; k < nv; ++k) r = r - cmul(hs[k], V[(long)k * ld + e]);
-        w[e] = r;
-        a += r.x * r.x + r.y * r.y;
-      }
+    for (int j = 0; j < CPP; ++j) r[j] = K::get(wv, j);
+    int k = 0;
+    for (; k + 4 <= nv; k += 4) {
+      typename K::P v4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v4[u] = __ldcs(reinterpret_cast<const typename K::P*>(V + (long)(k + u) * ld) + p);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < CPP; ++j) r[j] = r[j] - cmul(hs[k + u], K::get(v4[u], j));
     }
-    acc[0].x += (double)a;
+    for (; k < nv; ++k) {
+      const typename K::P v1 = __ldcs(reinterpret_cast<const typename K::P*>(V + (long)k * ld) + p);
+#pragma unroll
+      for (int j = 0; j < CPP; ++j) r[j] = r[j] - cmul(hs[k], K::get(v1, j));
+    }
+    wp[p] = K::make(r[0], r[CPP - 1]);
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < CPP; ++j) s += r[j].x * r[j].x + r[j].y * r[j].y;
+    an.add(mk<T>(s, 0));
   }
-  if (part) block_store<1>(acc, 1, part, nv);
+  if (CPP == 2 && (n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    C<T> r = w[n - 1];
+    for (int k = 0; k < nv; ++k) r = r - cmul(hs[k], V[(long)k * ld + n - 1]);
+    w[n - 1] = r;
+    an.add(mk<T>(r.x * r.x + r.y * r.y, 0));
+  }
+  const double2 s = block_sum(an.value(), red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!arrive_last(counter, gridDim.x)) return;
+  const double2 tot = sum_partials(part, gridDim.x, red);
+  if (threadIdx.x == 0) {
+    *out_norm = tot;
+    if (flag) *flag = (tot.x < eta2 * ref->x) ? 1 : 0;
+    *counter = 0u;
+  }
 }
 
+// ------------------------------------------------------------------ x += sum_k y_k V_k
 template <typename T>
 __global__ void __launch_bounds__(kKThreads) k_combine(const C<T>* __restrict__ V, long ld, int nv,
                                                       const double2* __restrict__ y, C<T>* __restrict__ x, long n) {
@@ -154,6 +248,7 @@ __global__ void __launch_bounds__(kKThreads) k_combine(const C<T>* __restrict__ 
   }
 }
 
+// dst = src * s, s = 1/sqrt(nrm2->x) (0 when the norm is 0) or host_scale when nrm2 is null
 template <typename T>
 __global__ void k_scale(const C<T>* __restrict__ src, C<T>* __restrict__ dst, long n, const double2* __restrict__ nrm2,
                         double host_scale) {
@@ -169,53 +264,31 @@ __global__ void k_scale(const C<T>* __restrict__ src, C<T>* __restrict__ dst, lo
   }
 }
 
+// out = |v|^2, or (b != null) y = b - y and out = |y|^2
 template <typename T>
-__global__ void __launch_bounds__(kKThreads) k_norm2(const C<T>* __restrict__ v, long n, double2* __restrict__ part,
-                                                    const C<T>* __restrict__ b, C<T>* __restrict__ y) {
-  // b == nullptr: |v|^2 ; otherwise y = b - y first and |y|^2
-  double2 acc[1] = {make_double2(0.0, 0.0)};
-  const long step = (long)gridDim.x * kKThreads * kChunk;
-  for (long base = (long)blockIdx.x * kKThreads * kChunk; base < n; base += step) {
-    T a = 0;
-#pragma unroll
-    for (int i = 0; i < kChunk; ++i) {
-      const long e = base + i * kKThreads + threadIdx.x;
-      if (e < n) {
-        C<T> r;
-        if (b) {
-          r = b[e] - y[e];
-          y[e] = r;
-        } else {
-          r = v[e];
-        }
-        a += r.x * r.x + r.y * r.y;
-      }
+__global__ void __launch_bounds__(kKThreads) k_norm2(const C<T>* __restrict__ v, long n, const C<T>* __restrict__ b,
+                                                    C<T>* __restrict__ y, double2* __restrict__ part,
+                                                    unsigned* __restrict__ counter, double2* __restrict__ out) {
+  __shared__ double2 red[kKThreads / 32];
+  Acc<T> an;
+  for (long e = (long)blockIdx.x * kKThreads + threadIdx.x; e < n; e += (long)gridDim.x * kKThreads) {
+    C<T> r;
+    if (b) {
+      r = b[e] - y[e];
+      y[e] = r;
+    } else {
+      r = v[e];
     }
-    acc[0].x += (double)a;
+    an.add(mk<T>(r.x * r.x + r.y * r.y, 0));
   }
-  block_store<1>(acc, 1, part, 0);
-}
-
-__global__ void k_reduce(const double2* __restrict__ part, int nblk, double2* __restrict__ out,
-                         double2* __restrict__ out2, const int* __restrict__ skip) {
-  if (skip && *skip == 0) return;
-  const int k = blockIdx.x;
-  double2 s = make_double2(0.0, 0.0);
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s = s + part[(long)k * kRedBlocks + b];
-  __shared__ double2 red[8];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
+  const double2 s = block_sum(an.value(), red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!arrive_last(counter, gridDim.x)) return;
+  const double2 tot = sum_partials(part, gridDim.x, red);
   if (threadIdx.x == 0) {
-    double2 t = make_double2(0.0, 0.0);
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = t + red[w];
-    out[k] = t;
-    if (out2) out2[k] = out2[k] + t;
+    *out = tot;
+    *counter = 0u;
   }
-}
-
-__global__ void k_reorth_flag(const double2* nb, const double2* na, double eta2, int* flag) {
-  *flag = (na->x < eta2 * nb->x) ? 1 : 0;
 }
 
 // ------------------------------------------------------------------ strided c128 / c64 helpers
@@ -245,71 +318,72 @@ __global__ void k_copy_c128(const double2* __restrict__ src, long scs, double2* 
     dst[c * dcs + e] = src[c * scs + e];
   }
 }
+// out = |a + b|^2 over a 3-component strided field (b optional, complex64)
 __global__ void __launch_bounds__(kKThreads) k_norm2_c128(const double2* __restrict__ a, long acs,
                                                          const float2* __restrict__ b, long bcs, long n,
-                                                         double2* __restrict__ part) {
-  double2 acc[1] = {make_double2(0.0, 0.0)};
+                                                         double2* __restrict__ part, unsigned* __restrict__ counter,
+                                                         double2* __restrict__ out) {
+  __shared__ double2 red[kKThreads / 32];
+  double2 acc = make_double2(0.0, 0.0);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 3 * n; i += (long)gridDim.x * blockDim.x) {
     const long c = i / n, e = i % n;
     double2 v = a[c * acs + e];
     if (b) v = v + to_c64(b[c * bcs + e]);
-    acc[0].x += v.x * v.x + v.y * v.y;
+    acc.x += v.x * v.x + v.y * v.y;
   }
-  block_store<1>(acc, 1, part, 0);
+  const double2 s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!arrive_last(counter, gridDim.x)) return;
+  const double2 tot = sum_partials(part, gridDim.x, red);
+  if (threadIdx.x == 0) {
+    *out = tot;
+    *counter = 0u;
+  }
 }
 
 // ------------------------------------------------------------------ launchers
 template <typename T>
-cudaError_t Krylov<T>::dots(const C<T>* V, long ld, int nv, const C<T>* w, long n, double2* part, bool with_norm,
-                            const int* skip, cudaStream_t s) {
+cudaError_t Krylov<T>::dots(const C<T>* V, long ld, int nv, const C<T>* w, long n, bool with_norm, double2* out,
+                            double2* acc, const int* skip, const RedScratch& sc, cudaStream_t s) {
+  if (nv < 1 || nv > kMaxBasis) return cudaErrorInvalidValue;
   dim3 grd(krylov_blocks(n), (nv + kDotGroup - 1) / kDotGroup);
-  if (nv == 0) grd.y = 1;
-  k_dots<T><<<grd, kKThreads, 0, s>>>(V, ld, nv, w, n, part, with_norm ? 1 : 0, skip);
+  k_dots<T><<<grd, kKThreads, 0, s>>>(V, ld, nv, w, n, with_norm ? 1 : 0, sc.part, sc.counters, out, acc, skip);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t Krylov<T>::update(const C<T>* V, long ld, int nv, const double2* h, C<T>* w, long n, double2* part,
-                              const int* skip, cudaStream_t s) {
-  if (nv > kMaxBasis) return cudaErrorInvalidValue;
-  k_update<T><<<krylov_blocks(n), kKThreads, 0, s>>>(V, ld, nv, h, w, n, part, skip);
+cudaError_t Krylov<T>::update(const C<T>* V, long ld, int nv, const double2* h, C<T>* w, long n, double2* out_norm,
+                              const double2* ref, double eta2, int* flag, const int* skip, const RedScratch& sc,
+                              cudaStream_t s) {
+  if (nv < 1 || nv > kMaxBasis) return cudaErrorInvalidValue;
+  k_update<T><<<krylov_blocks(n), kKThreads, 0, s>>>(V, ld, nv, h, w, n, sc.part, sc.counters + kCounterUpdate,
+                                                      out_norm, ref, eta2, flag, skip);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t Krylov<T>::combine(const C<T>* V, long ld, int nv, const double2* y, C<T>* x, long n, cudaStream_t s) {
   if (nv > kMaxBasis) return cudaErrorInvalidValue;
-  k_combine<T><<<krylov_blocks(n) * kChunk, kKThreads, 0, s>>>(V, ld, nv, y, x, n);
+  k_combine<T><<<krylov_blocks(n) * 2, kKThreads, 0, s>>>(V, ld, nv, y, x, n);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t Krylov<T>::scale(const C<T>* src, C<T>* dst, long n, const double* nrm2, double host_scale,
+cudaError_t Krylov<T>::scale(const C<T>* src, C<T>* dst, long n, const double2* nrm2, double host_scale,
                              cudaStream_t s) {
-  k_scale<T><<<krylov_blocks(n) * kChunk, kKThreads, 0, s>>>(src, dst, n, reinterpret_cast<const double2*>(nrm2),
-                                                             host_scale);
+  k_scale<T><<<krylov_blocks(n) * 2, kKThreads, 0, s>>>(src, dst, n, nrm2, host_scale);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t Krylov<T>::norm2(const C<T>* v, long n, double2* part, cudaStream_t s) {
-  k_norm2<T><<<krylov_blocks(n), kKThreads, 0, s>>>(v, n, part, nullptr, nullptr);
+cudaError_t Krylov<T>::norm2(const C<T>* v, long n, double2* out, const RedScratch& sc, cudaStream_t s) {
+  k_norm2<T><<<krylov_blocks(n), kKThreads, 0, s>>>(v, n, nullptr, nullptr, sc.part, sc.counters + kCounterNorm, out);
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t Krylov<T>::rsub(const C<T>* b, C<T>* y, long n, double2* part, cudaStream_t s) {
-  k_norm2<T><<<krylov_blocks(n), kKThreads, 0, s>>>(nullptr, n, part, b, y);
+cudaError_t Krylov<T>::rsub(const C<T>* b, C<T>* y, long n, double2* out, const RedScratch& sc, cudaStream_t s) {
+  k_norm2<T><<<krylov_blocks(n), kKThreads, 0, s>>>(nullptr, n, b, y, sc.part, sc.counters + kCounterNorm, out);
   return cudaGetLastError();
 }
 template struct Krylov<float>;
 template struct Krylov<double>;
 
-cudaError_t launch_reduce(const double2* part, int nblk, int nk, double2* out, double2* out2, const int* skip,
-                          cudaStream_t s) {
-  if (nk <= 0) return cudaSuccess;
-  k_reduce<<<nk, 256, 0, s>>>(part, nblk, out, out2, skip);
-  return cudaGetLastError();
-}
-cudaError_t launch_reorth_flag(const double2* nb, const double2* na, double eta2, int* flag, cudaStream_t s) {
-  k_reorth_flag<<<1, 1, 0, s>>>(nb, na, eta2, flag);
-  return cudaGetLastError();
-}
 static unsigned egrid(long n) {
   long g = (3 * n + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
@@ -331,9 +405,9 @@ cudaError_t launch_copy_c128(const double2* src, long scs, double2* dst, long dc
   k_copy_c128<<<egrid(n), 256, 0, s>>>(src, scs, dst, dcs, n);
   return cudaGetLastError();
 }
-cudaError_t launch_norm2_c128(const double2* a, long acs, const float2* b, long bcs, long n, double2* part,
-                              cudaStream_t s) {
-  k_norm2_c128<<<kRedBlocks, kKThreads, 0, s>>>(a, acs, b, bcs, n, part);
+cudaError_t launch_norm2_c128(const double2* a, long acs, const float2* b, long bcs, long n, double2* out,
+                              const RedScratch& sc, cudaStream_t s) {
+  k_norm2_c128<<<kRedBlocks, kKThreads, 0, s>>>(a, acs, b, bcs, n, sc.part, sc.counters + kCounterNorm, out);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,94 @@
+"""Small, fixed invocations of single parts of the path, for kernel profiling and quick timing.
+
+    python -m paper_2306_17537_gb300.kernel_cases matvec   --n 128 [--fp64] [--reps 5]
+        repeated sub-domain operator y = (I - G dsigma) x on an n^3 grid (five FFT passes)
+    python -m paper_2306_17537_gb300.kernel_cases gmres    --scale 2 [--iters 60]
+        one restarted GMRES(30) run on a sub-domain of the 128x128x256 workload divided by `scale`
+    python -m paper_2306_17537_gb300.kernel_cases solve    --scale 2
+        one complete forward solve (Algorithm 1) of the same workload
+
+Each prints the elapsed device time and the per-kernel-class accounting of the library.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def _ctx(grid, sigma0, freq, s6):
+    from . import ie
+
+    ctx = ie.Context(grid, grid.h, sigma0, freq)
+    ctx.set_contrast(s6)
+    return ctx
+
+
+def main(argv=None):
+    import torch
+
+    from . import ie, inputs
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["matvec", "gmres", "solve"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--scale", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--iters", type=int, default=60)
+    ap.add_argument("--fp64", action="store_true")
+    a = ap.parse_args(argv)
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"case": a.case}
+    if a.case == "matvec":
+        g = inputs.centred_grid(a.n, a.n, a.n, 0.25)
+        s6 = inputs.dipping_ti_with_ellipsoids(g, 0)
+        ctx = _ctx(g, 0.1, 4.0e5, s6)
+        ctx.set_stream(stream)
+        nb = 3 * g.n
+        if a.fp64:
+            x = inputs.random_field((3, g.nz, g.ny, g.nx), 1)
+            ctx.profile_enable(True)
+            for _ in range(a.reps):
+                ctx.matvec(x, precision=ie.IE_PREC_FP64)
+        else:
+            x = torch.randn(nb, dtype=torch.complex64, device=dev)
+            y = torch.empty_like(x)
+            ctx.matvec_dev(x, y)
+            torch.cuda.synchronize()
+            ctx.profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.reps):
+                ctx.matvec_dev(x, y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out["ms_per_matvec"] = e0.elapsed_time(e1) / a.reps
+    elif a.case == "gmres":
+        wl = inputs.config2(0, scale=a.scale)
+        ctx = _ctx(wl.grid, wl.sigma0, wl.freq, wl.sigma6)
+        nz = wl.grid.nz // 2
+        b = inputs.random_field((3, nz, wl.grid.ny, wl.grid.nx), 2)
+        ctx.profile_enable(True)
+        _, its, rr, st = ctx.gmres(b, nz=nz, tol=1e-14, restart=30, max_iter=a.iters,
+                                   precision=ie.IE_PREC_FP64 if a.fp64 else ie.IE_PREC_MIXED)
+        out.update({"iters": its, "rel_res": rr})
+    else:
+        wl = inputs.config2(0, scale=a.scale)
+        ctx = _ctx(wl.grid, wl.sigma0, wl.freq, wl.sigma6)
+        ctx.profile_enable(True)
+        H, info, st = ctx.solve(wl.sources, wl.receivers, ie.IE_DD_GAUSS_SEIDEL, wl.tol,
+                                ie.make_opts(z_split=wl.z_split, max_inner=4000, max_outer=60))
+        out.update({"sweeps": info.outer_iters, "gmres_iters": info.gmres_iters_total,
+                    "e": info.final_rel_residual, "seconds": info.seconds})
+    prof = ctx.profile_read()
+    out["kernels"] = {k: {"launches": v[0], "ms": round(v[1], 3), "GB": round(v[2] / 1e9, 4)}
+                      for k, v in prof.items() if v[0]}
+    print(json.dumps(out))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
