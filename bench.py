@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--scale", type=int, default=1, help="divide the grid by this factor (testing only)")
+    ap.add_argument("--restart", type=int, default=None, help="GMRES restart length (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -181,6 +182,8 @@ def run_gb300(args):
     ctx.set_stream(stream)
     setup_s = time.perf_counter() - t_setup0
     s6_dev = torch.from_numpy(np.ascontiguousarray(wl.sigma6)).to(dev)
+    if args.restart:
+        wl.restart = args.restart
     opts = ie.make_opts(z_split=wl.z_split, restart=wl.restart, precision=ie.IE_PREC_MIXED, max_inner=4000,
                         max_outer=60)
     src, rx = wl.sources, wl.receivers
@@ -303,7 +306,8 @@ def run_gb300(args):
                    "frac_of_peak": round(mv_bytes / 1e9 / (mv_ms / 1e3) / peak, 4),
                    "bytes_per_voxel": round(mv_bytes / n_block, 1)},
         "solve": {"status": int(st), "outer_iters": last.outer_iters, "gmres_iters": last.gmres_iters_total,
-                  "matvecs": last.matvecs, "final_rel_residual": last.final_rel_residual,
+                  "matvecs": last.matvecs, "reorth_passes": last.reorth_passes,
+                  "final_rel_residual": last.final_rel_residual,
                   "residual_history": [float(v) for v in last.history()],
                   "H_rx_z": [[float(H[0, r, 2].real), float(H[0, r, 2].imag)] for r in range(H.shape[1])]},
         "kernels": breakdown,

@@ -55,8 +55,9 @@ typedef enum {
 typedef enum { IE_DD_NONE = 0, IE_DD_JACOBI = 1, IE_DD_GAUSS_SEIDEL = 2 } ie_dd_mode;
 
 typedef enum {
-  IE_PREC_MIXED = 0, /* complex64 FFT convolution and Krylov vectors, FP64 outer residual/refinement */
-  IE_PREC_FP64 = 1   /* complex128 everywhere */
+  IE_PREC_MIXED = 0, /* complex64 FFT convolution and Krylov vectors; FP64-accurate outer residual/refinement */
+  IE_PREC_FP64 = 1,  /* complex128 everywhere */
+  IE_PREC_DFLOAT = 2 /* ie_matvec only: the double-float (FP32-pair, ~46-bit) kernels of the outer residual */
 } ie_precision;
 
 typedef struct {
@@ -90,6 +91,7 @@ typedef struct {
   double seconds;            /* wall time of the call */
   double residual_history[IE_MAX_HISTORY]; /* e before the first sweep and after each sweep */
   int32_t sweep_gmres_iters[IE_MAX_HISTORY]; /* GMRES iterations per sweep (first source) */
+  int32_t reorth_passes;     /* Arnoldi steps that needed a second Gram-Schmidt pass */
 } ie_info;
 
 typedef struct ie_ctx ie_ctx;

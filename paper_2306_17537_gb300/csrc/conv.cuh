@@ -10,11 +10,11 @@ enum Epilogue { EPI_APPLY = 0, EPI_ACCUM128 = 1, EPI_RESID128 = 2, EPI_CONV = 3 
 bool supported_pencil(int L);
 
 template <typename T> struct ConvLaunch {
-  static cudaError_t p1(int L, const C<T>* x, long x_cs, const T* ds, long d_cs, C<T>* A, long A_cs, int nx,
-                        long nrows, const C<T>* tw, cudaStream_t s);
-  static cudaError_t p5(int L, int mode, const C<T>* A, long A_cs, int nx, long nrows, const C<T>* xin, long x_cs,
-                        C<T>* y, long y_cs, double2* r, long r_cs, const double2* b, long b_cs, const C<T>* tw,
-                        cudaStream_t s);
+  static cudaError_t p1(int L, const FieldC<T>* x, long x_cs, const FieldR<T>* ds, long d_cs, C<T>* A, long A_cs,
+                        int nx, long nrows, const C<T>* tw, cudaStream_t s);
+  static cudaError_t p5(int L, int mode, const C<T>* A, long A_cs, int nx, long nrows, const FieldC<T>* xin,
+                        long x_cs, FieldC<T>* y, long y_cs, double2* r, long r_cs, const double2* b, long b_cs,
+                        const C<T>* tw, cudaStream_t s);
   static cudaError_t lanes(int L, int sign, const C<T>* in, long in_cs, long in_zs, long in_es, int n_in,
                            C<T>* out, long out_cs, long out_zs, long out_es, int n_out, int nlanes, int nbatch,
                            int ncomp, const C<T>* tw, cudaStream_t s);
@@ -24,5 +24,6 @@ template <typename T> struct ConvLaunch {
 };
 extern template struct ConvLaunch<float>;
 extern template struct ConvLaunch<double>;
+extern template struct ConvLaunch<df>;
 
 }  // namespace ie

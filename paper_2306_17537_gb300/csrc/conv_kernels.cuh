@@ -31,8 +31,9 @@ template <typename T, int L> struct LaneCfg {  // pencils strided, W neighbourin
 // ---------------------------------------------------------------- P1: J = dsigma x, x-FFT
 template <typename T, int L>
 __global__ void __launch_bounds__(kThreads) k_p1_contrast_fftx(
-    const C<T>* __restrict__ x, long x_cs, const T* __restrict__ ds, long d_cs,
+    const FieldC<T>* __restrict__ x, long x_cs, const FieldR<T>* __restrict__ ds, long d_cs,
     C<T>* __restrict__ A, long A_cs, int nx, long nrows, const C<T>* __restrict__ tw) {
+  using R = FieldR<T>;
   constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, P = RowCfg<T, L>::P;
   __shared__ C<T> smem[P * RowSM<T>::words(L)];
   const int t = threadIdx.x, p = threadIdx.y;
@@ -45,12 +46,12 @@ __global__ void __launch_bounds__(kThreads) k_p1_contrast_fftx(
     const int i = t + TT * m;
     if (act && i < nx) {
       const long o = row * nx + i;
-      const C<T> x0 = x[o], x1 = x[x_cs + o], x2 = x[2 * x_cs + o];
-      const T sxx = ds[o], syy = ds[d_cs + o], szz = ds[2 * d_cs + o];
-      const T sxy = ds[3 * d_cs + o], sxz = ds[4 * d_cs + o], syz = ds[5 * d_cs + o];
-      J[0][m] = mk<T>(sxx * x0.x + sxy * x1.x + sxz * x2.x, sxx * x0.y + sxy * x1.y + sxz * x2.y);
-      J[1][m] = mk<T>(sxy * x0.x + syy * x1.x + syz * x2.x, sxy * x0.y + syy * x1.y + syz * x2.y);
-      J[2][m] = mk<T>(sxz * x0.x + syz * x1.x + szz * x2.x, sxz * x0.y + syz * x1.y + szz * x2.y);
+      const FieldC<T> x0 = x[o], x1 = x[x_cs + o], x2 = x[2 * x_cs + o];
+      const R sxx = ds[o], syy = ds[d_cs + o], szz = ds[2 * d_cs + o];
+      const R sxy = ds[3 * d_cs + o], sxz = ds[4 * d_cs + o], syz = ds[5 * d_cs + o];
+      J[0][m] = to_c(mk<R>(sxx * x0.x + sxy * x1.x + sxz * x2.x, sxx * x0.y + sxy * x1.y + sxz * x2.y), T());
+      J[1][m] = to_c(mk<R>(sxy * x0.x + syy * x1.x + syz * x2.x, sxy * x0.y + syy * x1.y + syz * x2.y), T());
+      J[2][m] = to_c(mk<R>(sxz * x0.x + syz * x1.x + szz * x2.x, sxz * x0.y + syz * x1.y + szz * x2.y), T());
     } else {
       J[0][m] = J[1][m] = J[2][m] = czero<C<T>>();
     }
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(kThreads) k_p1_contrast_fftx(
 template <typename T, int L, int MODE>
 __global__ void __launch_bounds__(kThreads) k_p5_ifftx_epilogue(
     const C<T>* __restrict__ A, long A_cs, int nx, long nrows,
-    const C<T>* __restrict__ xin, long x_cs, C<T>* __restrict__ y, long y_cs,
+    const FieldC<T>* __restrict__ xin, long x_cs, FieldC<T>* __restrict__ y, long y_cs,
     double2* __restrict__ r, long r_cs, const double2* __restrict__ b, long b_cs,
     const C<T>* __restrict__ tw) {
   constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, P = RowCfg<T, L>::P;
@@ -89,9 +90,9 @@ __global__ void __launch_bounds__(kThreads) k_p5_ifftx_epilogue(
     if (i < nx) {
       const long o = row * nx + i;
       if constexpr (MODE == EPI_APPLY) {
-        y[c * y_cs + o] = xin[c * x_cs + o] - v[m];
+        y[c * y_cs + o] = xin[c * x_cs + o] - to_field(v[m]);
       } else if constexpr (MODE == EPI_CONV) {
-        y[c * y_cs + o] = v[m];
+        y[c * y_cs + o] = to_field(v[m]);
       } else if constexpr (MODE == EPI_ACCUM128) {
         r[c * r_cs + o] = r[c * r_cs + o] + to_c64(v[m]);
       } else {  // EPI_RESID128: r = b - x + G(dsigma x)
@@ -169,28 +170,41 @@ __global__ void __launch_bounds__(128, 4) k_p3_spectral(
 #pragma unroll
     for (int m = 0; m < E; ++m) sm.st(t + TT * m, v[m]);
   }
-  // Green product at the thread's own frequencies (no other thread touches these slots)
+  // Green product at the thread's own frequencies (no other thread touches these slots).
+  // The octant holds F[K_pq] for 0 <= k <= L/2 per axis; the full spectrum follows from the
+  // parities of K (diagonal components even, K_pq odd along p and q): with s_a = +-1 the side of
+  // axis a, F[K_pq](k) = s_p s_q F[K_pq](|k|), so Y_p = s_p sum_q F_pq(|k|) (s_q J_q). Register m of a
+  // pencil holds kz = t + TT*m, which lies in the lower half exactly when m < E/2 (the Nyquist
+  // frequency kz = L/2, where the odd components vanish, may take either side).
   {
-    const int ox = Lx / 2 + 1, oy = Ly / 2 + 1, oz = L / 2 + 1;
-    const long ocs = (long)oz * oy * ox;
+    const int ox = Lx / 2 + 1, oy = Ly / 2 + 1;
+    const long ocs = (long)(L / 2 + 1) * oy * ox, ozs = (long)oy * ox;
     const bool xlo = kx <= Lx / 2, ylo = ky <= Ly / 2;
     const int ix = xlo ? kx : Lx - kx, iy = ylo ? ky : Ly - ky;
-    const T sxy = (xlo == ylo) ? (T)1 : (T)-1;
+    const C<T>* gb = G + (long)iy * ox + ix;
     LaneSM<T, W> s0{spec[0] + w}, s1{spec[1] + w}, s2{spec[2] + w};
-#pragma unroll 4
-    for (int m = 0; m < E; ++m) {
-      const int kz = t + TT * m;
-      const bool zlo = kz <= L / 2;
-      const int iz = zlo ? kz : L - kz;
-      const T sxz = (xlo == zlo) ? (T)1 : (T)-1, syz = (ylo == zlo) ? (T)1 : (T)-1;
-      if (act) {
-        const C<T>* g = G + ((long)iz * oy + iy) * ox + ix;
-        const C<T> gxx = __ldg(g), gyy = __ldg(g + ocs), gzz = __ldg(g + 2 * ocs);
-        const C<T> gxy = sxy * __ldg(g + 3 * ocs), gxz = sxz * __ldg(g + 4 * ocs), gyz = syz * __ldg(g + 5 * ocs);
-        const C<T> j0 = s0.ld(kz), j1 = s1.ld(kz), j2 = s2.ld(kz);
-        s0.st(kz, cmul(gxx, j0) + cmul(gxy, j1) + cmul(gxz, j2));
-        s1.st(kz, cmul(gxy, j0) + cmul(gyy, j1) + cmul(gyz, j2));
-        s2.st(kz, cmul(gxz, j0) + cmul(gyz, j1) + cmul(gzz, j2));
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        constexpr int half = E / 2;
+        const bool zlo = (E == 1) || (m < half);
+        const int kz = t + TT * m, iz = zlo ? kz : L - kz;
+        const C<T>* g = gb + iz * ozs;
+        const C<T> gxx = ldgv(g), gyy = ldgv(g + ocs), gzz = ldgv(g + 2 * ocs);
+        const C<T> gxy = ldgv(g + 3 * ocs), gxz = ldgv(g + 4 * ocs), gyz = ldgv(g + 5 * ocs);
+        C<T> j0 = s0.ld(kz), j1 = s1.ld(kz), j2 = s2.ld(kz);
+        if (!xlo) j0 = mk<T>(-j0.x, -j0.y);
+        if (!ylo) j1 = mk<T>(-j1.x, -j1.y);
+        if (!zlo) j2 = mk<T>(-j2.x, -j2.y);
+        C<T> y0 = cmul(gxx, j0) + cmul(gxy, j1) + cmul(gxz, j2);
+        C<T> y1 = cmul(gxy, j0) + cmul(gyy, j1) + cmul(gyz, j2);
+        C<T> y2 = cmul(gxz, j0) + cmul(gyz, j1) + cmul(gzz, j2);
+        if (!xlo) y0 = mk<T>(-y0.x, -y0.y);
+        if (!ylo) y1 = mk<T>(-y1.x, -y1.y);
+        if (!zlo) y2 = mk<T>(-y2.x, -y2.y);
+        s0.st(kz, y0);
+        s1.st(kz, y1);
+        s2.st(kz, y2);
       }
     }
   }

@@ -22,8 +22,8 @@ inline bool supported_pencil_impl(int L) {
 
 
 template <typename T>
-cudaError_t ConvLaunch<T>::p1(int L, const C<T>* x, long x_cs, const T* ds, long d_cs, C<T>* A, long A_cs, int nx,
-                              long nrows, const C<T>* tw, cudaStream_t s) {
+cudaError_t ConvLaunch<T>::p1(int L, const FieldC<T>* x, long x_cs, const FieldR<T>* ds, long d_cs, C<T>* A,
+                              long A_cs, int nx, long nrows, const C<T>* tw, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   switch (L) {
 #define IE_CASE(N)                                                                              \
@@ -42,9 +42,9 @@ cudaError_t ConvLaunch<T>::p1(int L, const C<T>* x, long x_cs, const T* ds, long
 }
 
 template <typename T>
-cudaError_t ConvLaunch<T>::p5(int L, int mode, const C<T>* A, long A_cs, int nx, long nrows, const C<T>* xin,
-                              long x_cs, C<T>* y, long y_cs, double2* r, long r_cs, const double2* b, long b_cs,
-                              const C<T>* tw, cudaStream_t s) {
+cudaError_t ConvLaunch<T>::p5(int L, int mode, const C<T>* A, long A_cs, int nx, long nrows,
+                              const FieldC<T>* xin, long x_cs, FieldC<T>* y, long y_cs, double2* r, long r_cs,
+                              const double2* b, long b_cs, const C<T>* tw, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   switch (L) {
 #define IE_CASE(N)                                                                                               \

@@ -9,8 +9,8 @@
 // registers and the last stage writes registers, so a pencil of length E needs no shared memory and
 // a forward transform can be followed by pointwise work and the inverse transform in registers.
 //
-// E = 16 for float and 8 for double (register budget), so L = 256 in float is two radix-16 stages
-// with a single shared-memory exchange.
+// E = 16 for float and 8 for double and double-float (register budget), so L = 256 in float is two
+// radix-16 stages with a single shared-memory exchange.
 #pragma once
 #include "common.cuh"
 
@@ -19,6 +19,7 @@ namespace ie {
 template <typename T> struct EMax;
 template <> struct EMax<float> { static constexpr int v = 16; };
 template <> struct EMax<double> { static constexpr int v = 8; };
+template <> struct EMax<df> { static constexpr int v = 8; };
 
 template <typename T, int L> struct Plan {
   static constexpr int E = L < EMax<T>::v ? L : EMax<T>::v;  // elements per thread
@@ -94,7 +95,7 @@ template <typename T, int W> struct LaneSM {
 
 template <typename T, int SIGN>
 __device__ __forceinline__ C<T> twiddle(const C<T>* __restrict__ tw, int idx) {
-  C<T> w = __ldg(tw + idx);
+  C<T> w = ldgv(tw + idx);
   if (SIGN > 0) w.y = -w.y;
   return w;
 }

@@ -68,7 +68,7 @@ __global__ void k_green_tab(double2* __restrict__ out, int comp, int Lx, int Ly,
 }
 
 __global__ void k_extract_octant(const double2* __restrict__ full, int Lx, int Ly, int Lz, double scale,
-                                 double2* __restrict__ o64, float2* __restrict__ o32) {
+                                 double2* __restrict__ o64, float2* __restrict__ o32, float4* __restrict__ odf) {
   const int ox = Lx / 2 + 1, oy = Ly / 2 + 1, oz = Lz / 2 + 1;
   const long total = (long)ox * oy * oz;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
@@ -77,6 +77,8 @@ __global__ void k_extract_octant(const double2* __restrict__ full, int Lx, int L
     const double2 s = make_double2(scale * v.x, scale * v.y);
     o64[idx] = s;
     o32[idx] = make_float2((float)s.x, (float)s.y);
+    const df re(s.x), im(s.y);
+    odf[idx] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
 }
 
@@ -228,9 +230,10 @@ cudaError_t launch_green_tab(double2* out, int comp, int Lx, int Ly, int Lz, int
 }
 
 cudaError_t launch_extract_octant(const double2* full, int Lx, int Ly, int Lz, double scale, double2* o64,
-                                  float2* o32, cudaStream_t s) {
+                                  float2* o32, void* odf, cudaStream_t s) {
   const long n = (long)(Lx / 2 + 1) * (Ly / 2 + 1) * (Lz / 2 + 1);
-  k_extract_octant<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(full, Lx, Ly, Lz, scale, o64, o32);
+  k_extract_octant<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(full, Lx, Ly, Lz, scale, o64, o32,
+                                                               reinterpret_cast<float4*>(odf));
   return cudaGetLastError();
 }
 

@@ -9,8 +9,9 @@ constexpr int kMaxRx = 8;  // receivers handled per k_receivers launch
 
 cudaError_t launch_green_tab(double2* out, int comp, int Lx, int Ly, int Lz, int nx, int ny, int nz, double h,
                              double2 k, double sigma0, double2 self, cudaStream_t s);
+// octant of the scaled spectrum in complex128, complex64 and double-float (odf: [n] x 16 bytes)
 cudaError_t launch_extract_octant(const double2* full, int Lx, int Ly, int Lz, double scale, double2* o64,
-                                  float2* o32, cudaStream_t s);
+                                  float2* o32, void* odf, cudaStream_t s);
 cudaError_t launch_set_contrast(const double* s6, long N, double sigma0, double* d64, float* d32, int* bad,
                                 cudaStream_t s);
 cudaError_t launch_incident_E(double2* E0, int nx, int ny, int nz, const double* origin, double h, const double* pos,

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libie_gb300.so")
 
 IE_OK, IE_EINVAL, IE_ENOMEM, IE_ECUDA, IE_ENOCONV, IE_ESTATE = range(6)
 IE_DD_NONE, IE_DD_JACOBI, IE_DD_GAUSS_SEIDEL = range(3)
-IE_PREC_MIXED, IE_PREC_FP64 = range(2)
+IE_PREC_MIXED, IE_PREC_FP64, IE_PREC_DFLOAT = range(3)
 IE_MAX_HISTORY = 128
 KERNEL_CLASSES = ("P1_c64", "P2_c64", "P3_c64", "P4_c64", "P5_c64", "P1_c128", "P2_c128", "P3_c128", "P4_c128",
                   "P5_c128", "dots", "update", "krylov_misc", "field", "setup")
@@ -44,7 +44,7 @@ class ie_info(ct.Structure):
     _fields_ = [("outer_iters", ct.c_int32), ("gmres_iters_total", ct.c_int32), ("matvecs", ct.c_int32),
                 ("n_history", ct.c_int32), ("final_rel_residual", ct.c_double), ("seconds", ct.c_double),
                 ("residual_history", ct.c_double * IE_MAX_HISTORY),
-                ("sweep_gmres_iters", ct.c_int32 * IE_MAX_HISTORY)]
+                ("sweep_gmres_iters", ct.c_int32 * IE_MAX_HISTORY), ("reorth_passes", ct.c_int32)]
 
     def history(self):
         return list(self.residual_history[: self.n_history])

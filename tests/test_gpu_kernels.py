@@ -1,8 +1,9 @@
 """GPU parity of each hot-path step against the CPU FP64 oracle, called through the C ABI.
 
 Tolerances (relative L2 or max-abs over max):
-  * FP64 kernels (Green spectra, incident field, complex128 operator, interactions, receivers):
-    1e-11 — the same closed forms and FFT convolution in FP64, differing only in rounding order.
+  * FP64 kernels (Green spectra, incident field, complex128 operator, interactions, receivers) and
+    the double-float operator of the outer residual: 1e-11 — the same closed forms and FFT
+    convolution at (at least) 46-bit precision, differing only in rounding order.
   * complex64 operator: 1e-5 per matvec (FP32 FFT of length <= 1024 per axis has relative error
     ~ eps32 * log2(P) ~ 1e-6; the Green spectra are rounded from FP64).
 Shapes cover single cells, odd and prime sizes, non-power-of-two padding and several FFT tiles.
@@ -80,6 +81,16 @@ def test_operator_fp64_matches_oracle(ie, shape):
     x = inputs.random_field((3,) + shape, 5)
     ref = oop.FFTOperator(oop.contrast(s6, S0), g.h, F, S0)(x)
     assert rel(ctx.matvec(x, precision=ie.IE_PREC_FP64), ref) <= 1e-11
+    ctx.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_operator_double_float_matches_oracle(ie, shape):
+    # the FP64-accurate whole-grid residual runs on these FP32-pair kernels (about 46-bit arithmetic)
+    ctx, g, s6 = _ctx(ie, shape, seed=2)
+    x = inputs.random_field((3,) + shape, 5)
+    ref = oop.FFTOperator(oop.contrast(s6, S0), g.h, F, S0)(x)
+    assert rel(ctx.matvec(x, precision=ie.IE_PREC_DFLOAT), ref) <= 1e-11
     ctx.close()
 
 
