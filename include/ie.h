@@ -141,6 +141,20 @@ ie_status ie_matvec(ie_ctx* ctx, int32_t precision, int32_t z0, int32_t nz, cons
  * enqueued on the context stream without synchronising. */
 ie_status ie_matvec_dev(ie_ctx* ctx, int32_t z0, int32_t nz, const void* x_dev, void* y_dev);
 
+/* Same operator as ie_matvec_dev, for callers that must not allocate device memory during the call:
+ * code running while a CUDA stream is being captured, real-time loops with a fixed memory budget, or
+ * hosts whose allocator is owned by someone else. (An extension of this library; the paper has no
+ * counterpart.) The FFT intermediates go to one fixed 16 MiB device array that the library reserves
+ * on every GPU it is loaded on; slabs needing more (24 * nz * Lx * (ny + Ly) bytes, Lx/Ly the padded
+ * FFT lengths) are rejected with IE_EINVAL. The Green spectra for the slab height must already exist
+ * (ie_create prepares the whole grid; otherwise call ie_matvec_dev once first), else IE_ESTATE.
+ * The first call on each device looks up the array's device address; make that call before any
+ * stream capture. All calls share the array: calls that overlap on the GPU (different streams or
+ * contexts at the same time) race and give wrong results. Nothing in it needs clearing between
+ * calls. x_dev, y_dev: distinct device arrays [3][nz][ny][nx] complex64; work is enqueued on the
+ * context stream without synchronising. */
+ie_status ie_matvec_dev_noalloc(ie_ctx* ctx, int32_t z0, int32_t nz, const void* x_dev, void* y_dev);
+
 /* Interaction field of eqs. 21/23: y = G^(ts) dsigma^(s) x for a source slab [zs0, zs0+nzs) and a
  * target slab [zt0, zt0+nzt), computed with the whole-grid spectra (complex128 kernels). x: source
  * field [3][nzs][ny][nx], y: target field [3][nzt][ny][nx], host, complex. */

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1040,3 +1041,75 @@ void ie_destroy(ie_ctx* c) {
 }
 
 }  // extern "C"
+
+// =============================================================================== no-allocation operator
+// Scratch of ie_matvec_dev_noalloc: the x-transformed (A) and xy-transformed (B) intermediates of the
+// five FFT passes live in this fixed device array instead of context workspaces, so the call never
+// allocates. Every GPU that loads the library reserves it for the life of the process.
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device, looked up once per device.
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" ie_status ie_matvec_dev_noalloc(ie_ctx* c, int32_t z0, int32_t nz, const void* x_dev, void* y_dev) {
+  if (!c || !x_dev || !y_dev || x_dev == y_dev) return fail(c, IE_EINVAL, "bad argument");
+  if (z0 < 0 || nz < 1 || z0 + nz > c->nz) return fail(c, IE_EINVAL, "slab outside the grid");
+  if (!c->has_contrast) return fail(c, IE_ESTATE, "no contrast set");
+  const SpecSet* S = nullptr;
+  for (auto* sp : c->specs)
+    if (sp->nz_set == nz) S = sp;
+  if (!S)
+    return fail(c, IE_ESTATE,
+                "no Green spectra for this slab height yet: ie_create prepares the whole grid; other heights are "
+                "prepared by one ie_matvec_dev or ie_solve call first");
+  const size_t a_bytes = sizeof(float2) * 3 * (size_t)nz * c->ny * c->Lx;
+  const size_t b_off = (a_bytes + 255) & ~size_t(255);
+  const size_t need = b_off + sizeof(float2) * 3 * (size_t)nz * c->Ly * c->Lx;
+  if (need > kNoAllocScratchBytes)
+    return fail(c, IE_EINVAL,
+                "slab needs " + std::to_string(need) + " bytes of scratch, above the " +
+                    std::to_string(kNoAllocScratchBytes) + "-byte limit of the no-allocation operator");
+  void* base = nullptr;
+  CK(noalloc_scratch(&base));
+  float2* A = reinterpret_cast<float2*>(base);
+  float2* B = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(base) + b_off);
+  const float2* x = reinterpret_cast<const float2*>(x_dev);
+  float2* y = reinterpret_cast<float2*>(y_dev);
+  const long nb = (long)nz * c->ny * c->nx, nxy = (long)c->nx * c->ny;
+  const long A_cs = (long)nz * c->ny * c->Lx, B_cs = (long)nz * c->Ly * c->Lx;
+  const float2* tw = c->tw32.as<float2>();
+  cudaStream_t s = c->stream;
+  // the five passes of the sub-domain operator; every scratch element they read was written first,
+  // so nothing needs clearing between calls
+  CK(ConvLaunch<float>::p1(c->Lx, x, nb, c->ds32.as<float>() + (long)z0 * nxy, c->N, A, A_cs, c->nx,
+                           (long)nz * c->ny, tw, s));
+  CK(ConvLaunch<float>::lanes(c->Ly, -1, A, A_cs, (long)c->ny * c->Lx, c->Lx, c->ny, B, B_cs, (long)c->Ly * c->Lx,
+                              c->Lx, c->Ly, c->Lx, nz, 3, tw, s));
+  CK(ConvLaunch<float>::p3(S->Lz, B, B_cs, nz, 0, B, B_cs, nz, 0, S->G32.as<float2>(), c->Lx, c->Ly, tw, s));
+  CK(ConvLaunch<float>::lanes(c->Ly, +1, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx,
+                              c->Lx, c->ny, c->Lx, nz, 3, tw, s));
+  CK(ConvLaunch<float>::p5(c->Lx, EPI_APPLY, A, A_cs, c->nx, (long)nz * c->ny, x, nb, y, nb, nullptr, 0, nullptr, 0,
+                           tw, s));
+  return IE_OK;
+}

@@ -67,6 +67,7 @@ _SIGS = {
     "ie_get_field": (ct.c_int, [_P, _D]),
     "ie_matvec": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_int32, _D, _D]),
     "ie_matvec_dev": (ct.c_int, [_P, ct.c_int32, ct.c_int32, _P, _P]),
+    "ie_matvec_dev_noalloc": (ct.c_int, [_P, ct.c_int32, ct.c_int32, _P, _P]),
     "ie_interaction": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, _D, _D]),
     "ie_gmres": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_int32, _D, _D, ct.c_double, ct.c_int32, ct.c_int32, _D,
                             ct.POINTER(ct.c_int32), _D]),
@@ -199,6 +200,11 @@ class Context:
     def matvec_dev(self, x_dev, y_dev, z0=0, nz=None):
         nz = self.nz if nz is None else nz
         self._check(_lib.ie_matvec_dev(self.ptr, int(z0), int(nz), _P(_addr(x_dev)), _P(_addr(y_dev))))
+
+    def matvec_dev_noalloc(self, x_dev, y_dev, z0=0, nz=None):
+        """ie_matvec_dev without any device allocation (fixed 16 MiB library scratch; see ie.h)."""
+        nz = self.nz if nz is None else nz
+        self._check(_lib.ie_matvec_dev_noalloc(self.ptr, int(z0), int(nz), _P(_addr(x_dev)), _P(_addr(y_dev))))
 
     def interaction(self, x: np.ndarray, zs0, nzs, zt0, nzt) -> np.ndarray:
         xx = _c128(x, 3 * nzs * self.ny * self.nx)
