@@ -42,6 +42,13 @@ template <typename V> __host__ __device__ __forceinline__ V cmul_conjb(V a, V b)
   return r;
 }
 template <typename V> __host__ __device__ __forceinline__ V czero() { V r; r.x = 0; r.y = 0; return r; }
+// real scalar times complex
+template <typename S, typename V> __host__ __device__ __forceinline__ V cscale(S s, V a) {
+  V r;
+  r.x = s * a.x;
+  r.y = s * a.y;
+  return r;
+}
 
 __device__ __forceinline__ float2 to_c(double2 a, float) { return make_float2((float)a.x, (float)a.y); }
 __device__ __forceinline__ double2 to_c(double2 a, double) { return a; }

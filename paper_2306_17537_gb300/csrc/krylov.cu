@@ -48,14 +48,31 @@ template <> struct Acc<float> {    // Kahan-compensated FP32
     c.y = (ti - s.y) - yi;
     s.y = ti;
   }
-  __device__ __forceinline__ double2 value() const {
-    return make_double2((double)s.x - (double)c.x, (double)s.y - (double)c.y);
+  // Sum over the warp in double-float (FP32 pipes; compensation kept), converted to FP64 once.
+  __device__ __forceinline__ double2 warp_total() const {
+    df re(s.x, -c.x), im(s.y, -c.y);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const df r2(__shfl_down_sync(0xffffffffu, re.hi, o), __shfl_down_sync(0xffffffffu, re.lo, o));
+      const df i2(__shfl_down_sync(0xffffffffu, im.hi, o), __shfl_down_sync(0xffffffffu, im.lo, o));
+      re = re + r2;
+      im = im + i2;
+    }
+    return make_double2(to_double(re), to_double(im));
   }
 };
 template <> struct Acc<double> {
   double2 s = make_double2(0.0, 0.0);
   __device__ __forceinline__ void add(double2 x) { s = s + x; }
-  __device__ __forceinline__ double2 value() const { return s; }
+  __device__ __forceinline__ double2 warp_total() const {
+    double2 v = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+  }
 };
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
@@ -67,18 +84,22 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
   return v;
 }
 
-// Sum one value per thread over the block (FP64); result valid in thread 0.
-__device__ __forceinline__ double2 block_sum(double2 v, double2* red /* [kKThreads/32] shared */) {
+// Sum the warp totals over the block in FP64 (lane 0 of each warp holds one); result in thread 0.
+__device__ __forceinline__ double2 block_sum_warps(double2 wt, double2* red /* [kKThreads/32] shared */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
   __syncthreads();
-  if (lane == 0) red[warp] = v;
+  if (lane == 0) red[warp] = wt;
   __syncthreads();
   double2 s = make_double2(0.0, 0.0);
   if (threadIdx.x == 0)
     for (int w = 0; w < kKThreads / 32; ++w) s = s + red[w];
   return s;
 }
+template <typename T> __device__ __forceinline__ double2 block_sum(const Acc<T>& a, double2* red) {
+  return block_sum_warps(a.warp_total(), red);
+}
+// Sum one FP64 value per thread over the block; result in thread 0.
+__device__ __forceinline__ double2 block_sum(double2 v, double2* red) { return block_sum_warps(warp_sum(v), red); }
 
 // Last-block detection after this block has written its partials.
 __device__ __forceinline__ bool arrive_last(unsigned* counter, unsigned nblocks) {
@@ -153,12 +174,12 @@ __global__ void __launch_bounds__(kKThreads) k_dots(const C<T>* __restrict__ V, 
 #pragma unroll
   for (int q = 0; q < G; ++q) {
     if (q < nk) {
-      const double2 s = block_sum(a[q].value(), red);
+      const double2 s = block_sum(a[q], red);
       if (threadIdx.x == 0) part[(long)(k0 + q) * kRedBlocks + blockIdx.x] = s;
     }
   }
   if (dn) {
-    const double2 s = block_sum(an.value(), red);
+    const double2 s = block_sum(an, red);
     if (threadIdx.x == 0) part[(long)nv * kRedBlocks + blockIdx.x] = s;
   }
   if (!arrive_last(counters + g, gridDim.x)) return;
@@ -223,7 +244,7 @@ __global__ void __launch_bounds__(kKThreads) k_update(const C<T>* __restrict__ V
     w[n - 1] = r;
     an.add(mk<T>(r.x * r.x + r.y * r.y, 0));
   }
-  const double2 s = block_sum(an.value(), red);
+  const double2 s = block_sum(an, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   if (!arrive_last(counter, gridDim.x)) return;
   const double2 tot = sum_partials(part, gridDim.x, red);
@@ -281,7 +302,7 @@ __global__ void __launch_bounds__(kKThreads) k_norm2(const C<T>* __restrict__ v,
     }
     an.add(mk<T>(r.x * r.x + r.y * r.y, 0));
   }
-  const double2 s = block_sum(an.value(), red);
+  const double2 s = block_sum(an, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   if (!arrive_last(counter, gridDim.x)) return;
   const double2 tot = sum_partials(part, gridDim.x, red);
