@@ -61,6 +61,28 @@ def dist_env():
     return rank, world, local
 
 
+# ------------------------------------------------------------------------------------ ranks
+def rank_seed(seed: int, rank: int) -> int:
+    """Weak scaling: every rank solves its own tool position (an independent seeded model)."""
+    return seed + rank
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over all ranks (timings: the job is as slow as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps: int, world: int, t_ms_max: float) -> float:
+    """Whole-job solves per second: all ranks' steps over the slowest rank's time."""
+    return steps * world / (t_ms_max / 1000.0)
+
+
 # ------------------------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -174,7 +196,7 @@ def run_gb300(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     # weak scaling: every rank solves its own tool position (independent model seed), no data exchange
-    wl = inputs.config2(args.seed + rank, scale=args.scale)
+    wl = inputs.config2(rank_seed(args.seed, rank), scale=args.scale)
     g = wl.grid
     t_setup0 = time.perf_counter()
     ctx = ie.Context(g, g.h, wl.sigma0, wl.freq)
@@ -215,11 +237,8 @@ def run_gb300(args):
     t_ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read()
     ctx.profile_enable(False)
-    tmax = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    t_ms_max = float(tmax.item())
-    value = args.steps * world / (t_ms_max / 1000.0)
+    t_ms_max = max_over_ranks(t_ms, dev)
+    value = job_throughput(args.steps, world, t_ms_max)
     # ----------------------------------------------------------------- end to end (host buffers)
     s6_pin = torch.from_numpy(np.ascontiguousarray(wl.sigma6)).pin_memory()
     s6_host = s6_pin.numpy()
@@ -234,10 +253,7 @@ def run_gb300(args):
         H2, info2, _ = ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, opts)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    te = torch.tensor([e0.elapsed_time(e1)], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = e2e_steps * world / (float(te.item()) / 1000.0)
+    e2e_value = job_throughput(e2e_steps, world, max_over_ranks(e0.elapsed_time(e1), dev))
     h2d = s6_host.nbytes + rx.nbytes + 48 * len(src)
     d2h = H2.nbytes
     # ----------------------------------------------------------------- block operator bandwidth
