@@ -1,7 +1,8 @@
 """Small, fixed invocations of single parts of the path, for kernel profiling and quick timing.
 
-    python -m paper_2306_17537_gb300.kernel_cases matvec   --n 128 [--fp64] [--reps 5]
-        repeated sub-domain operator y = (I - G dsigma) x on an n^3 grid (five FFT passes)
+    python -m paper_2306_17537_gb300.kernel_cases matvec   --n 128 [--fp64 | --dfloat] [--reps 5]
+        repeated sub-domain operator y = (I - G dsigma) x on an n^3 grid (five FFT passes), complex64
+        by default, complex128 or double-float (the outer-residual kernels) on request
     python -m paper_2306_17537_gb300.kernel_cases gmres    --scale 2 [--iters 60]
         one restarted GMRES(30) run on a sub-domain of the 128x128x256 workload divided by `scale`
     python -m paper_2306_17537_gb300.kernel_cases solve    --scale 2
@@ -37,6 +38,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--iters", type=int, default=60)
     ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--dfloat", action="store_true")
     a = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -48,11 +50,11 @@ def main(argv=None):
         ctx = _ctx(g, 0.1, 4.0e5, s6)
         ctx.set_stream(stream)
         nb = 3 * g.n
-        if a.fp64:
+        if a.fp64 or a.dfloat:
             x = inputs.random_field((3, g.nz, g.ny, g.nx), 1)
             ctx.profile_enable(True)
             for _ in range(a.reps):
-                ctx.matvec(x, precision=ie.IE_PREC_FP64)
+                ctx.matvec(x, precision=ie.IE_PREC_FP64 if a.fp64 else ie.IE_PREC_DFLOAT)
         else:
             x = torch.randn(nb, dtype=torch.complex64, device=dev)
             y = torch.empty_like(x)
