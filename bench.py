@@ -327,6 +327,7 @@ def run_gb300(args):
                   "residual_history": [float(v) for v in last.history()],
                   "H_rx_z": [[float(H[0, r, 2].real), float(H[0, r, 2].imag)] for r in range(H.shape[1])]},
         "kernels": breakdown,
+        "tuned_tiles": ie.tuned_tiles().strip().splitlines(),
         "gpu_launches": gpu_launches,
         "clocks": clk,
         "cpu_baseline": cpu_baseline,

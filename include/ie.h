@@ -128,6 +128,32 @@ ie_status ie_set_contrast_dev(ie_ctx* ctx, const double* sigma6_dev);
 ie_status ie_solve(ie_ctx* ctx, int32_t n_src, const ie_dipole* src, int32_t n_rx, const double* rx_xyz,
                    int32_t dd_mode, double tol, const ie_opts* opts, double* H_out, ie_info* info);
 
+/* One forward problem of a batch: inputs as for ie_solve, outputs written by ie_solve_batch. */
+typedef struct {
+  ie_ctx* ctx;             /* context of the item (grid, cell size, background, frequency, contrast) */
+  const double* sigma6;    /* host [nz][ny][nx][6] conductivity set before the solve, or NULL to keep
+                              the context's current model */
+  int32_t n_src;
+  const ie_dipole* src;
+  int32_t n_rx;
+  const double* rx_xyz;    /* [n_rx][3] */
+  int32_t dd_mode;
+  double tol;
+  const ie_opts* opts;     /* may be NULL */
+  double* H_out;           /* [n_src][n_rx][3] complex */
+  ie_info* info;           /* may be NULL */
+  ie_status status;        /* result of this item */
+} ie_batch_item;
+
+/* Many independent forward problems (tool positions x frequencies, Section 3.3's moving window) in
+ * flight together. Items that share a context run one after another in the given order; different
+ * contexts run concurrently, each on its own CUDA stream driven by one of up to max_concurrent host
+ * threads (0: one per distinct context, at most 16), so their kernels overlap on the GPU. A context
+ * still on the legacy default stream gets a private non-blocking stream for the call. Every item's
+ * status is written; the call returns IE_OK if all items did, else the first non-OK status in item
+ * order. An item without sigma6 uses the contrast already set on its context. */
+ie_status ie_solve_batch(int32_t n_items, ie_batch_item* items, int32_t max_concurrent);
+
 /* Copy the electric field of the last source of the last ie_solve to the host ([3][nz][ny][nx]
  * complex, interleaved). IE_ESTATE if no solve has run. */
 ie_status ie_get_field(ie_ctx* ctx, double* E_out);
@@ -206,6 +232,12 @@ ie_status ie_profile_enable(ie_ctx* ctx, int32_t on);
 /* Counters of one class since the last ie_profile_enable: launches, device milliseconds (0 unless
  * timing was on) and algorithmic bytes. Any output pointer may be NULL. */
 ie_status ie_profile_read(const ie_ctx* ctx, int32_t kclass, int64_t* launches, double* ms, double* algo_bytes);
+
+/* Tile shapes chosen so far by the FFT-tile autotuner of this process, as text (one line per pass
+ * shape: pass, element bytes, pencil length, Lx, Ly, slab heights, chosen variant; variant 1 = half the
+ * pencils per block). Writes at most len bytes including the terminating NUL; returns the length the
+ * full text needs. */
+int32_t ie_tuned_tiles(char* buf, int32_t len);
 
 /* Last error message of the context (never NULL; "" when none). */
 const char* ie_last_error(const ie_ctx* ctx);

@@ -8,6 +8,7 @@ namespace ie {
 enum Epilogue { EPI_APPLY = 0, EPI_ACCUM128 = 1, EPI_RESID128 = 2, EPI_CONV = 3 };
 
 bool supported_pencil(int L);
+constexpr int kTileVariants = 2;
 
 template <typename T> struct ConvLaunch {
   static cudaError_t p1(int L, const FieldC<T>* x, long x_cs, const FieldR<T>* ds, long d_cs, C<T>* A, long A_cs,
@@ -15,11 +16,12 @@ template <typename T> struct ConvLaunch {
   static cudaError_t p5(int L, int mode, const C<T>* A, long A_cs, int nx, long nrows, const FieldC<T>* xin,
                         long x_cs, FieldC<T>* y, long y_cs, double2* r, long r_cs, const double2* b, long b_cs,
                         const C<T>* tw, cudaStream_t s);
-  static cudaError_t lanes(int L, int sign, const C<T>* in, long in_cs, long in_zs, long in_es, int n_in,
-                           C<T>* out, long out_cs, long out_zs, long out_es, int n_out, int nlanes, int nbatch,
-                           int ncomp, const C<T>* tw, cudaStream_t s);
-  static cudaError_t p3(int L, const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt,
-                        int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, cudaStream_t s);
+  // variant: 0 = default tile, 1 = half the lanes per block (choices for the autotuner)
+  static cudaError_t lanes(int L, int sign, int variant, const C<T>* in, long in_cs, long in_zs, long in_es,
+                           int n_in, C<T>* out, long out_cs, long out_zs, long out_es, int n_out, int nlanes,
+                           int nbatch, int ncomp, const C<T>* tw, cudaStream_t s);
+  static cudaError_t p3(int L, int variant, const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs,
+                        int nzt, int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, cudaStream_t s);
   static cudaError_t rows(int L, int sign, C<T>* data, long nrows, const C<T>* tw, cudaStream_t s);
 };
 extern template struct ConvLaunch<float>;

@@ -22,9 +22,11 @@ template <typename T, int L> struct RowCfg {  // pencils contiguous in memory (x
   static constexpr int P0 = kThreads / TT;
   static constexpr int P = P0 < 1 ? 1 : (P0 > 64 ? 64 : P0);  // pencils per block
 };
-template <typename T, int L> struct LaneCfg {  // pencils strided, W neighbouring pencils per block
+// Pencils strided, W neighbouring pencils (lanes) per block. WDIV = 2 is the narrower tile the
+// autotuner may pick (half the lanes, half the threads per block).
+template <typename T, int L, int WDIV = 1> struct LaneCfg {
   static constexpr int TT = Plan<T, L>::TT;
-  static constexpr int W0 = kThreads / TT;
+  static constexpr int W0 = kThreads / TT / WDIV;
   static constexpr int W = W0 < 1 ? 1 : (W0 > 32 ? 32 : W0);
 };
 
@@ -104,12 +106,12 @@ __global__ void __launch_bounds__(kThreads) k_p5_ifftx_epilogue(
 
 // ---------------------------------------------------------------- strided FFT (P2, P4, setup)
 // Pencil element e of lane `lane`, batch z, component c sits at c*cs + z*zs + e*es + lane.
-template <typename T, int L, int SIGN>
+template <typename T, int L, int SIGN, int WDIV>
 __global__ void __launch_bounds__(kThreads) k_lanes_fft(
     const C<T>* __restrict__ in, long in_cs, long in_zs, long in_es, int n_in,
     C<T>* __restrict__ out, long out_cs, long out_zs, long out_es, int n_out, int nlanes,
     const C<T>* __restrict__ tw) {
-  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = LaneCfg<T, L>::W;
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = LaneCfg<T, L, WDIV>::W;
   __shared__ C<T> smem[L * W];
   const int w = threadIdx.x, t = threadIdx.y;
   const long z = blockIdx.y, c = blockIdx.z;
@@ -140,17 +142,17 @@ __global__ void __launch_bounds__(kThreads) k_lanes_fft(
 // The three forward spectra are kept in shared memory (one buffer per component, also used for that
 // component's FFT exchanges), so a thread holds one pencil in registers at a time: 128-thread blocks
 // with 48 KB of shared memory, four blocks per SM.
-template <typename T, int L> struct P3Cfg {
+template <typename T, int L, int WDIV = 1> struct P3Cfg {
   static constexpr int TT = Plan<T, L>::TT;
-  static constexpr int W0 = 128 / TT;
+  static constexpr int W0 = 128 / TT / WDIV;
   static constexpr int W = W0 < 1 ? 1 : (W0 > 32 ? 32 : W0);
 };
 
-template <typename T, int L>
+template <typename T, int L, int WDIV>
 __global__ void __launch_bounds__(128, 4) k_p3_spectral(
     const C<T>* __restrict__ Bin, long in_cs, int nzs, int os, C<T>* __restrict__ Bout, long out_cs,
     int nzt, int ot, const C<T>* __restrict__ G, int Lx, int Ly, const C<T>* __restrict__ tw) {
-  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = P3Cfg<T, L>::W;
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = P3Cfg<T, L, WDIV>::W;
   __shared__ C<T> spec[3][L * W];
   const int w = threadIdx.x, t = threadIdx.y;
   const int kx = blockIdx.x * W + w, ky = blockIdx.y;

@@ -81,49 +81,63 @@ cudaError_t ConvLaunch<T>::p5(int L, int mode, const C<T>* A, long A_cs, int nx,
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t ConvLaunch<T>::lanes(int L, int sign, const C<T>* in, long in_cs, long in_zs, long in_es, int n_in,
-                                 C<T>* out, long out_cs, long out_zs, long out_es, int n_out, int nlanes, int nbatch,
-                                 int ncomp, const C<T>* tw, cudaStream_t s) {
-  if (nbatch <= 0 || nlanes <= 0 || ncomp <= 0) return cudaSuccess;
-  switch (L) {
-#define IE_CASE(N)                                                                                               \
-  case N: {                                                                                                      \
-    constexpr int W = LaneCfg<T, N>::W;                                                                          \
-    dim3 blk(W, Plan<T, N>::TT), grd((unsigned)((nlanes + W - 1) / W), (unsigned)nbatch, (unsigned)ncomp);      \
-    if (sign < 0)                                                                                                \
-      k_lanes_fft<T, N, -1><<<grd, blk, 0, s>>>(in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es,      \
-                                                 n_out, nlanes, tw);                                             \
-    else                                                                                                         \
-      k_lanes_fft<T, N, 1><<<grd, blk, 0, s>>>(in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es,       \
-                                                n_out, nlanes, tw);                                              \
-    break;                                                                                                       \
-  }
-    IE_FOR_EACH_L(IE_CASE)
-#undef IE_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
+template <typename T, int N, int WDIV>
+static cudaError_t lanes_launch(int sign, const C<T>* in, long in_cs, long in_zs, long in_es, int n_in, C<T>* out,
+                                long out_cs, long out_zs, long out_es, int n_out, int nlanes, int nbatch, int ncomp,
+                                const C<T>* tw, cudaStream_t s) {
+  constexpr int W = LaneCfg<T, N, WDIV>::W;
+  dim3 blk(W, Plan<T, N>::TT), grd((unsigned)((nlanes + W - 1) / W), (unsigned)nbatch, (unsigned)ncomp);
+  if (sign < 0)
+    k_lanes_fft<T, N, -1, WDIV><<<grd, blk, 0, s>>>(in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out,
+                                                     nlanes, tw);
+  else
+    k_lanes_fft<T, N, 1, WDIV><<<grd, blk, 0, s>>>(in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out,
+                                                    nlanes, tw);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t ConvLaunch<T>::p3(int L, const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt,
-                              int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, cudaStream_t s) {
+cudaError_t ConvLaunch<T>::lanes(int L, int sign, int variant, const C<T>* in, long in_cs, long in_zs, long in_es,
+                                 int n_in, C<T>* out, long out_cs, long out_zs, long out_es, int n_out, int nlanes,
+                                 int nbatch, int ncomp, const C<T>* tw, cudaStream_t s) {
+  if (nbatch <= 0 || nlanes <= 0 || ncomp <= 0) return cudaSuccess;
   switch (L) {
-#define IE_CASE(N)                                                                                            \
-  case N: {                                                                                                   \
-    constexpr int W = P3Cfg<T, N>::W;                                                                         \
-    dim3 blk(W, Plan<T, N>::TT), grd((unsigned)((Lx + W - 1) / W), (unsigned)Ly);                            \
-    k_p3_spectral<T, N><<<grd, blk, 0, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw);       \
-    break;                                                                                                    \
-  }
+#define IE_CASE(N)                                                                                                 \
+  case N:                                                                                                          \
+    return variant ? lanes_launch<T, N, 2>(sign, in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out, \
+                                           nlanes, nbatch, ncomp, tw, s)                                          \
+                   : lanes_launch<T, N, 1>(sign, in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out, \
+                                           nlanes, nbatch, ncomp, tw, s);
     IE_FOR_EACH_L(IE_CASE)
 #undef IE_CASE
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+template <typename T, int N, int WDIV>
+static cudaError_t p3_launch(const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt, int ot,
+                             const C<T>* G, int Lx, int Ly, const C<T>* tw, cudaStream_t s) {
+  constexpr int W = P3Cfg<T, N, WDIV>::W;
+  dim3 blk(W, Plan<T, N>::TT), grd((unsigned)((Lx + W - 1) / W), (unsigned)Ly);
+  k_p3_spectral<T, N, WDIV><<<grd, blk, 0, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ConvLaunch<T>::p3(int L, int variant, const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout,
+                              long out_cs, int nzt, int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw,
+                              cudaStream_t s) {
+  switch (L) {
+#define IE_CASE(N)                                                                                             \
+  case N:                                                                                                      \
+    return variant ? p3_launch<T, N, 2>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, s)          \
+                   : p3_launch<T, N, 1>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, s);
+    IE_FOR_EACH_L(IE_CASE)
+#undef IE_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 template <typename T>

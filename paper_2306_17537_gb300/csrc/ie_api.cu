@@ -12,12 +12,16 @@
 // With IE_PREC_MIXED the block GMRES runs on complex64 vectors with complex64 FFT convolutions and
 // the FP64 residual carries the accuracy; with IE_PREC_FP64 everything is complex128.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <tuple>
 #include <vector>
 
 #include "conv.cuh"
@@ -224,12 +228,12 @@ ie_status get_spec(ie_ctx* c, int nz_set, SpecSet** out) {
              [&]() { return ConvLaunch<double>::rows(c->Lx, -1, F, (long)Lz * c->Ly, tw, c->stream); });
     if (e == cudaSuccess)  // y: element e of lane x in plane z at z*Ly*Lx + e*Lx + x
       e = kl(c, IE_K_SETUP, 32.0 * vol, [&]() {
-        return ConvLaunch<double>::lanes(c->Ly, -1, F, 0, (long)c->Ly * c->Lx, c->Lx, c->Ly, F, 0,
+        return ConvLaunch<double>::lanes(c->Ly, -1, 0, F, 0, (long)c->Ly * c->Lx, c->Lx, c->Ly, F, 0,
                                          (long)c->Ly * c->Lx, c->Lx, c->Ly, c->Lx, Lz, 1, tw, c->stream);
       });
     if (e == cudaSuccess)  // z: element e of lane x in row y at y*Lx + e*Ly*Lx + x
       e = kl(c, IE_K_SETUP, 32.0 * vol, [&]() {
-        return ConvLaunch<double>::lanes(Lz, -1, F, 0, c->Lx, (long)c->Ly * c->Lx, Lz, F, 0, c->Lx,
+        return ConvLaunch<double>::lanes(Lz, -1, 0, F, 0, c->Lx, (long)c->Ly * c->Lx, Lz, F, 0, c->Lx,
                                          (long)c->Ly * c->Lx, Lz, c->Lx, c->Ly, 1, tw, c->stream);
       });
     if (e == cudaSuccess)
@@ -264,6 +268,55 @@ template <typename T> ie_status ensure_conv_ws(ie_ctx* c, int zcap) {
   return IE_OK;
 }
 
+// ------------------------------------------------------------------ FFT tile autotuner
+// The strided passes (P2, P3, P4) have two tile shapes (kTileVariants): the default and one with half
+// the pencils per block. The first convolution of a new shape times every variant on the live buffers
+// (three timed launches each after a warm-up; the work is data independent) and keeps the fastest for
+// the rest of the process. Variants produce bit-identical results.
+struct TuneKey {
+  int kind, bytes, L, Lx, Ly, nz, nz2;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kind, bytes, L, Lx, Ly, nz, nz2) < std::tie(o.kind, o.bytes, o.L, o.Lx, o.Ly, o.nz, o.nz2);
+  }
+};
+std::map<TuneKey, int> g_tuned;
+std::mutex g_tune_mu;
+
+int tuned_variant(const TuneKey& k) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(k);
+  return it == g_tuned.end() ? -1 : it->second;
+}
+
+// Time each variant of one launch (run(v) enqueues it on the context stream) and record the fastest.
+template <class F> cudaError_t tune(ie_ctx* c, const TuneKey& k, F&& run, int* best) {
+  cudaEvent_t a, b;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  float best_ms = 1e30f;
+  *best = 0;
+  for (int v = 0; v < kTileVariants && e == cudaSuccess; ++v) {
+    e = run(v);  // warm-up (module load, caches)
+    if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = run(v);
+    if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      *best = v;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[k] = *best;
+  }
+  return e;
+}
+
 // One FFT convolution G^(ts) dsigma^(s) x with the given spectra and epilogue (see conv_kernels.cuh).
 //   x: source field, components at stride x_cs, covering the slab [zs0, zs0 + nzs) of the grid;
 //   os/ot: pencil positions of the source / target slab inside the padded z axis of `S`.
@@ -284,16 +337,36 @@ ie_status conv(ie_ctx* c, const SpecSet* S, const FieldC<T>* x, long x_cs, int z
   const double fz = sizeof(FieldC<T>), rz = sizeof(FieldR<T>);
   const double epi = mode == EPI_APPLY ? 2 * fz : mode == EPI_CONV ? fz : mode == EPI_ACCUM128 ? 32.0 : 32.0 + fz;
   const int k0 = cls_base<T>();
-  KL(k0 + 0, (3 * fz + 6 * rz) * nzs * nxy + 3 * sz * nzs * c->ny * c->Lx,
-     ConvLaunch<T>::p1(c->Lx, x, x_cs, dsig<T>(c) + (long)zs0 * nxy, c->N, A, A_cs, c->nx, (long)nzs * c->ny, tw, s));
-  KL(k0 + 1, 3 * sz * nzs * c->Lx * (double)(c->ny + c->Ly),
-     ConvLaunch<T>::lanes(c->Ly, -1, A, A_cs, (long)c->ny * c->Lx, c->Lx, c->ny, B, B_cs, (long)c->Ly * c->Lx, c->Lx,
-                          c->Ly, c->Lx, nzs, 3, tw, s));
-  KL(k0 + 2, 3 * sz * (double)(nzs + nzt) * c->Ly * c->Lx + 6 * sz * ocs,
-     ConvLaunch<T>::p3(S->Lz, B, B_cs, nzs, os, B, B_cs, nzt, ot, spec<T>(S), c->Lx, c->Ly, tw, s));
-  KL(k0 + 3, 3 * sz * nzt * c->Lx * (double)(c->Ly + c->ny),
-     ConvLaunch<T>::lanes(c->Ly, +1, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx, c->Lx,
-                          c->ny, c->Lx, nzt, 3, tw, s));
+  const int bz = (int)sizeof(C<T>) + (std::is_same<T, df>::value ? 1 : 0);  // tells the three arithmetics apart
+  const TuneKey k2{2, bz, c->Ly, c->Lx, c->ny, nzs, 0}, k3{3, bz, S->Lz, c->Lx, c->Ly, nzs, nzt},
+      k4{4, bz, c->Ly, c->Lx, c->ny, nzt, 0};
+  auto p1 = [&]() {
+    return ConvLaunch<T>::p1(c->Lx, x, x_cs, dsig<T>(c) + (long)zs0 * nxy, c->N, A, A_cs, c->nx, (long)nzs * c->ny, tw,
+                             s);
+  };
+  auto p2 = [&](int v) {
+    return ConvLaunch<T>::lanes(c->Ly, -1, v, A, A_cs, (long)c->ny * c->Lx, c->Lx, c->ny, B, B_cs, (long)c->Ly * c->Lx,
+                                c->Lx, c->Ly, c->Lx, nzs, 3, tw, s);
+  };
+  auto p3 = [&](int v) {
+    return ConvLaunch<T>::p3(S->Lz, v, B, B_cs, nzs, os, B, B_cs, nzt, ot, spec<T>(S), c->Lx, c->Ly, tw, s);
+  };
+  auto p4 = [&](int v) {
+    return ConvLaunch<T>::lanes(c->Ly, +1, v, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx,
+                                c->Lx, c->ny, c->Lx, nzt, 3, tw, s);
+  };
+  KL(k0 + 0, (3 * fz + 6 * rz) * nzs * nxy + 3 * sz * nzs * c->ny * c->Lx, p1());
+  int v2 = tuned_variant(k2), v3 = tuned_variant(k3), v4 = tuned_variant(k4);
+  if (v2 < 0) CK(tune(c, k2, p2, &v2));
+  KL(k0 + 1, 3 * sz * nzs * c->Lx * (double)(c->ny + c->Ly), p2(v2));
+  if (v3 < 0) {  // P3 works in place: tune on the live B, then rebuild B from x before the real pass
+    CK(tune(c, k3, p3, &v3));
+    CK(p1());
+    CK(p2(v2));
+  }
+  KL(k0 + 2, 3 * sz * (double)(nzs + nzt) * c->Ly * c->Lx + 6 * sz * ocs, p3(v3));
+  if (v4 < 0) CK(tune(c, k4, p4, &v4));
+  KL(k0 + 3, 3 * sz * nzt * c->Lx * (double)(c->Ly + c->ny), p4(v4));
   KL(k0 + 4, 3 * sz * nzt * c->ny * c->Lx + 3 * epi * nzt * nxy,
      ConvLaunch<T>::p5(c->Lx, mode, A, A_cs, c->nx, (long)nzt * c->ny, xin, xin_cs, y, y_cs, r, r_cs, b, b_cs, tw, s));
   return IE_OK;
@@ -876,6 +949,71 @@ ie_status ie_solve(ie_ctx* c, int32_t n_src, const ie_dipole* src, int32_t n_rx,
   return worst;
 }
 
+ie_status ie_solve_batch(int32_t n_items, ie_batch_item* items, int32_t max_concurrent) {
+  if (n_items < 0 || (n_items > 0 && !items) || max_concurrent < 0) return IE_EINVAL;
+  // group items by context, keeping the given order inside each group
+  std::vector<ie_ctx*> ctxs;
+  std::vector<std::vector<int>> groups;
+  for (int i = 0; i < n_items; ++i) {
+    items[i].status = IE_ESTATE;
+    if (!items[i].ctx) {
+      items[i].status = IE_EINVAL;
+      continue;
+    }
+    size_t g = 0;
+    while (g < ctxs.size() && ctxs[g] != items[i].ctx) ++g;
+    if (g == ctxs.size()) {
+      ctxs.push_back(items[i].ctx);
+      groups.emplace_back();
+    }
+    groups[g].push_back(i);
+  }
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return IE_ECUDA;
+  // private non-blocking streams for contexts on the legacy default stream
+  std::vector<cudaStream_t> owned(ctxs.size(), nullptr), saved(ctxs.size(), nullptr);
+  for (size_t g = 0; g < ctxs.size(); ++g) {
+    saved[g] = ctxs[g]->stream;
+    if (!saved[g]) {
+      if (cudaStreamCreateWithFlags(&owned[g], cudaStreamNonBlocking) != cudaSuccess) {
+        for (size_t h = 0; h < g; ++h)
+          if (owned[h]) cudaStreamDestroy(owned[h]);
+        return IE_ECUDA;
+      }
+      ctxs[g]->stream = owned[g];
+    }
+  }
+  int workers = max_concurrent > 0 ? max_concurrent : (int)std::min<size_t>(ctxs.size(), 16);
+  workers = std::max(1, std::min<int>(workers, (int)std::max<size_t>(ctxs.size(), 1)));
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    cudaSetDevice(device);
+    for (int g; (g = next.fetch_add(1)) < (int)groups.size();) {
+      for (int i : groups[g]) {
+        ie_batch_item& it = items[i];
+        it.status = it.sigma6 ? ie_set_contrast(it.ctx, it.sigma6) : IE_OK;
+        if (it.status == IE_OK)
+          it.status = ie_solve(it.ctx, it.n_src, it.src, it.n_rx, it.rx_xyz, it.dd_mode, it.tol, it.opts, it.H_out,
+                               it.info);
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+  for (size_t g = 0; g < ctxs.size(); ++g) {
+    if (owned[g]) {
+      cudaStreamSynchronize(owned[g]);
+      cudaStreamDestroy(owned[g]);
+      ctxs[g]->stream = saved[g];
+    }
+  }
+  for (int i = 0; i < n_items; ++i)
+    if (items[i].status != IE_OK) return items[i].status;
+  return IE_OK;
+}
+
 ie_status ie_get_field(ie_ctx* c, double* E_out) {
   if (!c || !E_out) return fail(c, IE_EINVAL, "null argument");
   if (!c->has_field) return fail(c, IE_ESTATE, "no solve has run");
@@ -1032,6 +1170,26 @@ ie_status ie_profile_read(const ie_ctx* cc, int32_t kclass, int64_t* launches, d
   return IE_OK;
 }
 
+int32_t ie_tuned_tiles(char* buf, int32_t len) {
+  std::string txt;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    static const char* pass[] = {"", "", "P2", "P3", "P4"};
+    for (const auto& kv : g_tuned) {
+      const TuneKey& k = kv.first;
+      txt += std::string(pass[k.kind]) + " bytes=" + std::to_string(k.bytes) + " L=" + std::to_string(k.L) +
+             " Lx=" + std::to_string(k.Lx) + " Ly=" + std::to_string(k.Ly) + " nz=" + std::to_string(k.nz) + "/" +
+             std::to_string(k.nz2) + " variant=" + std::to_string(kv.second) + "\n";
+    }
+  }
+  if (buf && len > 0) {
+    const size_t n = std::min<size_t>(txt.size(), (size_t)len - 1);
+    std::memcpy(buf, txt.data(), n);
+    buf[n] = 0;
+  }
+  return (int32_t)txt.size() + 1;
+}
+
 const char* ie_last_error(const ie_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 void ie_destroy(ie_ctx* c) {
@@ -1104,10 +1262,10 @@ extern "C" ie_status ie_matvec_dev_noalloc(ie_ctx* c, int32_t z0, int32_t nz, co
   // so nothing needs clearing between calls
   CK(ConvLaunch<float>::p1(c->Lx, x, nb, c->ds32.as<float>() + (long)z0 * nxy, c->N, A, A_cs, c->nx,
                            (long)nz * c->ny, tw, s));
-  CK(ConvLaunch<float>::lanes(c->Ly, -1, A, A_cs, (long)c->ny * c->Lx, c->Lx, c->ny, B, B_cs, (long)c->Ly * c->Lx,
+  CK(ConvLaunch<float>::lanes(c->Ly, -1, 0, A, A_cs, (long)c->ny * c->Lx, c->Lx, c->ny, B, B_cs, (long)c->Ly * c->Lx,
                               c->Lx, c->Ly, c->Lx, nz, 3, tw, s));
-  CK(ConvLaunch<float>::p3(S->Lz, B, B_cs, nz, 0, B, B_cs, nz, 0, S->G32.as<float2>(), c->Lx, c->Ly, tw, s));
-  CK(ConvLaunch<float>::lanes(c->Ly, +1, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx,
+  CK(ConvLaunch<float>::p3(S->Lz, 0, B, B_cs, nz, 0, B, B_cs, nz, 0, S->G32.as<float2>(), c->Lx, c->Ly, tw, s));
+  CK(ConvLaunch<float>::lanes(c->Ly, +1, 0, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx,
                               c->Lx, c->ny, c->Lx, nz, 3, tw, s));
   CK(ConvLaunch<float>::p5(c->Lx, EPI_APPLY, A, A_cs, c->nx, (long)nz * c->ny, x, nb, y, nb, nullptr, 0, nullptr, 0,
                            tw, s));

@@ -40,6 +40,13 @@ class ie_opts(ct.Structure):
                 ("adaptive", ct.c_int32), ("fixed_tol", ct.c_double)]
 
 
+class ie_batch_item(ct.Structure):
+    _fields_ = [("ctx", ct.c_void_p), ("sigma6", ct.POINTER(ct.c_double)), ("n_src", ct.c_int32),
+                ("src", ct.POINTER(ie_dipole)), ("n_rx", ct.c_int32), ("rx_xyz", ct.POINTER(ct.c_double)),
+                ("dd_mode", ct.c_int32), ("tol", ct.c_double), ("opts", ct.POINTER(ie_opts)),
+                ("H_out", ct.POINTER(ct.c_double)), ("info", ct.c_void_p), ("status", ct.c_int)]
+
+
 class ie_info(ct.Structure):
     _fields_ = [("outer_iters", ct.c_int32), ("gmres_iters_total", ct.c_int32), ("matvecs", ct.c_int32),
                 ("n_history", ct.c_int32), ("final_rel_residual", ct.c_double), ("seconds", ct.c_double),
@@ -65,6 +72,7 @@ _SIGS = {
     "ie_solve": (ct.c_int, [_P, ct.c_int32, ct.POINTER(ie_dipole), ct.c_int32, _D, ct.c_int32, ct.c_double,
                             ct.POINTER(ie_opts), _D, ct.POINTER(ie_info)]),
     "ie_get_field": (ct.c_int, [_P, _D]),
+    "ie_solve_batch": (ct.c_int, [ct.c_int32, ct.POINTER(ie_batch_item), ct.c_int32]),
     "ie_matvec": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_int32, _D, _D]),
     "ie_matvec_dev": (ct.c_int, [_P, ct.c_int32, ct.c_int32, _P, _P]),
     "ie_matvec_dev_noalloc": (ct.c_int, [_P, ct.c_int32, ct.c_int32, _P, _P]),
@@ -77,6 +85,7 @@ _SIGS = {
     "ie_fft_dims": (ct.c_int, [_P, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "ie_profile_enable": (ct.c_int, [_P, ct.c_int32]),
     "ie_profile_read": (ct.c_int, [_P, ct.c_int32, ct.POINTER(ct.c_int64), _D, _D]),
+    "ie_tuned_tiles": (ct.c_int32, [ct.c_char_p, ct.c_int32]),
     "ie_last_error": (ct.c_char_p, [_P]),
     "ie_destroy": (None, [_P]),
 }
@@ -267,6 +276,45 @@ class Context:
         dims = (ct.c_int32 * 3)()
         self._check(_lib.ie_fft_dims(self.ptr, int(self.nz if nz_set is None else nz_set), dims))
         return tuple(dims)
+
+
+def solve_batch(problems, max_concurrent=0):
+    """ie_solve_batch on a list of dicts with keys ctx (Context), sources, receivers and optionally
+    sigma6 (host array set on the context before that item), dd_mode, tol, opts. Items sharing a
+    context run in order; different contexts run concurrently. Returns [(H, info, status)]."""
+    n = len(problems)
+    items = (ie_batch_item * max(1, n))()
+    keep, outs = [], []
+    for i, p in enumerate(problems):
+        ctx = p["ctx"]
+        src = (ie_dipole * max(1, len(p["sources"])))(*[_dipole(d) for d in p["sources"]])
+        rx = np.ascontiguousarray(np.asarray(p["receivers"], dtype=np.float64).reshape(-1, 3))
+        H = np.zeros((len(p["sources"]), len(rx), 3), dtype=np.complex128)
+        info = ie_info()
+        s6 = p.get("sigma6")
+        s6 = np.ascontiguousarray(s6, dtype=np.float64) if s6 is not None else None
+        it = items[i]
+        it.ctx = ctx.ptr
+        it.sigma6 = _dptr(s6) if s6 is not None else None
+        it.n_src, it.src = len(p["sources"]), src
+        it.n_rx, it.rx_xyz = len(rx), _dptr(rx)
+        it.dd_mode, it.tol = int(p.get("dd_mode", IE_DD_NONE)), float(p.get("tol", 1e-6))
+        o = p.get("opts")
+        it.opts = ct.pointer(o) if o is not None else None
+        it.H_out = _dptr(H)
+        it.info = ct.cast(ct.pointer(info), ct.c_void_p)
+        keep += [src, rx, s6, o, info]
+        outs.append((H, info))
+    _lib.ie_solve_batch(n, items, int(max_concurrent))
+    return [(H, info, items[i].status) for i, (H, info) in enumerate(outs)]
+
+
+def tuned_tiles() -> str:
+    """Tile shapes chosen so far by the library's FFT-tile autotuner (ie_tuned_tiles)."""
+    n = _lib.ie_tuned_tiles(None, 0)
+    buf = ct.create_string_buffer(n)
+    _lib.ie_tuned_tiles(buf, n)
+    return buf.value.decode()
 
 
 def make_opts(n_blocks=1, z_split=None, restart=30, max_outer=50, max_inner=600, precision=IE_PREC_MIXED,

@@ -204,6 +204,97 @@ def config2(seed: int = 0, scale: int = 1) -> Workload:
                     z_split=[0, nz // 2, nz], tol=1e-6, restart=40)
 
 
+@dataclass
+class Formation:
+    """A layered earth model in global coordinates (z up) in the style of the paper's logging example
+    (Section 3.3): anisotropic shale layers around isotropic sand layers, a fault offsetting the stack,
+    and the exponential perturbation of the sand conductivity
+    sigma_sand = sigma_u (1 + alpha exp(-|r - r_c| / gamma))."""
+    normal: np.ndarray  # unit layer normal (global)
+    interfaces: np.ndarray  # sorted offsets of the layer boundaries along the normal, metres
+    sigma_h: np.ndarray
+    sigma_v: np.ndarray
+    is_sand: np.ndarray
+    fault_point: np.ndarray
+    fault_normal: np.ndarray
+    fault_throw: float  # offset of the layer stack (along the layer normal) across the fault plane
+    r_c: np.ndarray  # centre of the sand perturbation
+    alpha: float
+    gamma: float
+
+
+def formation(seed: int, n_layers: int = 7, extent: float = 80.0) -> Formation:
+    """Seeded logging formation: layers dipping U(0, 30) deg, alternately shale (TI, sigma_h
+    10^U(-0.5, 0.3) S/m, anisotropy ratio U(2, 5)) and sand (isotropic 10^U(-2, -1) S/m) with the
+    exponential perturbation (alpha = 4, gamma = 50 m, as in Section 3.3), and a planar fault."""
+    rng = np.random.default_rng(seed)
+    th, ph = np.deg2rad(rng.uniform(0.0, 30.0)), rng.uniform(0.0, 2.0 * np.pi)
+    nrm = np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    iface = np.sort(rng.uniform(-extent / 4, extent / 4, n_layers - 1))
+    sand = (np.arange(n_layers) % 2) == 1
+    sh = np.where(sand, 10.0 ** rng.uniform(-2.0, -1.0, n_layers), 10.0 ** rng.uniform(-0.5, 0.3, n_layers))
+    sv = np.where(sand, sh, sh / rng.uniform(2.0, 5.0, n_layers))
+    fth, fph = np.deg2rad(rng.uniform(50.0, 80.0)), rng.uniform(0.0, 2.0 * np.pi)
+    fn = np.array([np.sin(fth) * np.cos(fph), np.sin(fth) * np.sin(fph), np.cos(fth)])
+    return Formation(nrm, iface, sh, sv, sand, rng.uniform(-5.0, 5.0, 3), fn, float(rng.uniform(1.0, 4.0)),
+                     rng.uniform(-extent / 3, extent / 3, 3), 4.0, 50.0)
+
+
+def window_sigma6(form: Formation, grid: Grid, tool_pos, rot) -> np.ndarray:
+    """Conductivity of ``form`` on a tool-aligned window grid: the columns of ``rot`` are the tool
+    axes in global coordinates (tool z along the well), the window origin is relative to ``tool_pos``.
+    Layer tensors are rotated into the tool frame by Appendix C using the tool-frame layer normal."""
+    xc, yc, zc = grid.centres()
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+    loc = np.stack([X, Y, Z], axis=-1)
+    glob = np.asarray(tool_pos) + loc @ rot.T
+    side = np.sign((glob - form.fault_point) @ form.fault_normal)
+    dist = glob @ form.normal + 0.5 * form.fault_throw * side
+    layer = np.searchsorted(form.interfaces, dist)
+    pert = 1.0 + form.alpha * np.exp(-np.linalg.norm(glob - form.r_c, axis=-1) / form.gamma)
+    factor = np.where(form.is_sand[layer], pert, 1.0)
+    n_tool = rot.T @ form.normal
+    theta = np.arccos(np.clip(n_tool[2], -1.0, 1.0))
+    phi = np.arctan2(n_tool[1], n_tool[0])
+    return ti_tensor(form.sigma_h[layer] * factor, form.sigma_v[layer] * factor, theta, phi)
+
+
+def trajectory(seed: int, n_positions: int, spacing: float = 0.5):
+    """Seeded deviated well: inclination U(60, 85) deg from vertical, random azimuth; returns tool
+    positions and the tool-frame rotation (columns: tool x, y, z axes in global coordinates)."""
+    rng = np.random.default_rng(seed + 1000)
+    inc, az = np.deg2rad(rng.uniform(60.0, 85.0)), rng.uniform(0.0, 2.0 * np.pi)
+    d = np.array([np.sin(inc) * np.cos(az), np.sin(inc) * np.sin(az), np.cos(inc)])
+    ex = np.cross([0.0, 0.0, 1.0], d)
+    ex /= np.linalg.norm(ex)
+    ey = np.cross(d, ex)
+    rot = np.stack([ex, ey, d], axis=1)
+    start = -0.5 * spacing * (n_positions - 1) * d
+    return [start + k * spacing * d for k in range(n_positions)], rot
+
+
+# Tool-aligned windows of the batched logging workload: (shape (nz, ny, nx), sub-domain split along z)
+LOGGING_WINDOWS = {
+    2.0e6: ((160, 64, 64), [0, 64, 160]),     # 64^3 + 64x64x96 sub-domains
+    1.0e5: ((320, 128, 128), [0, 128, 320]),  # 128^3 + 128x128x192 sub-domains
+}
+
+
+def config3_item(seed: int, position: int, freq: float, n_positions: int = 64, scale: int = 1) -> Workload:
+    """One (tool position, frequency) problem of the batched logging workload: a window of the seeded
+    formation around position ``position`` of the seeded trajectory, coaxial z-dipole tool, block
+    Jacobi over two uneven sub-domains along the tool axis, tol 1e-6. ``scale`` > 1 shrinks the window."""
+    (nz, ny, nx), split = LOGGING_WINDOWS[freq]
+    nz, ny, nx = nz // scale, ny // scale, nx // scale
+    split = [v // scale for v in split]
+    g = centred_grid(nx, ny, nz, 0.25)
+    pos, rot = trajectory(seed, n_positions)
+    s6 = window_sigma6(formation(seed), g, pos[position], rot)
+    src, rx = coaxial_tool()
+    name = f"logging window {nx}x{ny}x{nz} @0.25 m, position {position}, {freq:g} Hz"
+    return Workload(name, g, 0.1, freq, s6, src, rx, z_split=split, tol=1e-6, restart=40)
+
+
 def random_contrast_sigma6(shape, seed: int, sigma0: float, spread: float = 0.5) -> np.ndarray:
     """Random symmetric positive-definite conductivity around sigma0 (for operator parity tests)."""
     rng = np.random.default_rng(seed)

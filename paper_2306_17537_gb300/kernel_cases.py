@@ -7,6 +7,9 @@
         one restarted GMRES(30) run on a sub-domain of the 128x128x256 workload divided by `scale`
     python -m paper_2306_17537_gb300.kernel_cases solve    --scale 2
         one complete forward solve (Algorithm 1) of the same workload
+    python -m paper_2306_17537_gb300.kernel_cases batch    --positions 8 [--scale 1] [--lanes 4]
+        the batched logging workload: positions x {100 kHz, 2 MHz} tool-aligned windows, block Jacobi,
+        solved with ie_solve_batch (lanes contexts per frequency), then one at a time for comparison
 
 Each prints the elapsed device time and the per-kernel-class accounting of the library.
 """
@@ -32,7 +35,10 @@ def main(argv=None):
     from . import ie, inputs
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["matvec", "gmres", "solve"])
+    ap.add_argument("case", choices=["matvec", "gmres", "solve", "batch"])
+    ap.add_argument("--positions", type=int, default=8)
+    ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--freqs", default="1e5,2e6", help="batch case: comma-separated frequencies")
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--scale", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
@@ -77,6 +83,35 @@ def main(argv=None):
         _, its, rr, st = ctx.gmres(b, nz=nz, tol=1e-14, restart=30, max_iter=a.iters,
                                    precision=ie.IE_PREC_FP64 if a.fp64 else ie.IE_PREC_MIXED)
         out.update({"iters": its, "rel_res": rr})
+    elif a.case == "batch":
+        import time
+
+        scale = a.scale if a.scale > 0 else 1
+        freqs = [float(v) for v in a.freqs.split(",")]
+        probs = [inputs.config3_item(0, p, f, n_positions=a.positions, scale=scale)
+                 for f in freqs for p in range(a.positions)]
+        ctxs = {}
+        for w in probs:
+            lst = ctxs.setdefault(w.freq, [])
+            if len(lst) < a.lanes:
+                lst.append(ie.Context(w.grid, w.grid.h, w.sigma0, w.freq))
+        batch, count = [], {}
+        for w in probs:
+            k = count.get(w.freq, 0)
+            count[w.freq] = k + 1
+            batch.append(dict(ctx=ctxs[w.freq][k % a.lanes], sigma6=w.sigma6, sources=w.sources,
+                              receivers=w.receivers, dd_mode=ie.IE_DD_JACOBI, tol=w.tol,
+                              opts=ie.make_opts(z_split=w.z_split, restart=w.restart, max_inner=4000, max_outer=60)))
+        ie.solve_batch(batch[:2])  # warm-up: spectra of every sub-domain height, tile tuning
+        for mode, conc in (("concurrent", 0), ("one at a time", 1)):
+            t0 = time.perf_counter()
+            res = ie.solve_batch(batch, max_concurrent=conc)
+            dt = time.perf_counter() - t0
+            out[mode] = {"solves": len(batch), "seconds": round(dt, 3), "solves_per_s": round(len(batch) / dt, 4),
+                         "all_ok": all(r[2] == ie.IE_OK for r in res),
+                         "max_rel_residual": max(r[1].final_rel_residual for r in res),
+                         "gmres_iters": [r[1].gmres_iters_total for r in res]}
+        ctx = next(iter(ctxs.values()))[0]
     else:
         wl = inputs.config2(0, scale=a.scale)
         ctx = _ctx(wl.grid, wl.sigma0, wl.freq, wl.sigma6)
@@ -85,6 +120,7 @@ def main(argv=None):
                                 ie.make_opts(z_split=wl.z_split, max_inner=4000, max_outer=60))
         out.update({"sweeps": info.outer_iters, "gmres_iters": info.gmres_iters_total,
                     "e": info.final_rel_residual, "seconds": info.seconds})
+    out["tuned_tiles"] = ie.tuned_tiles().strip().splitlines()
     prof = ctx.profile_read()
     out["kernels"] = {k: {"launches": v[0], "ms": round(v[1], 3), "GB": round(v[2] / 1e9, 4)}
                       for k, v in prof.items() if v[0]}
