@@ -92,6 +92,9 @@ typedef struct {
   double residual_history[IE_MAX_HISTORY]; /* e before the first sweep and after each sweep */
   int32_t sweep_gmres_iters[IE_MAX_HISTORY]; /* GMRES iterations per sweep (first source) */
   int32_t reorth_passes;     /* Arnoldi steps that needed a second Gram-Schmidt pass */
+  int32_t warm_start_used;   /* 1 if the guess of ie_set_initial_field_dev replaced E := E0 */
+  double cold_rel_residual;  /* with a guess given: e (eq. 9) of E = E0 and of the guess; else 0 */
+  double warm_rel_residual;
 } ie_info;
 
 typedef struct ie_ctx ie_ctx;
@@ -157,6 +160,18 @@ ie_status ie_solve_batch(int32_t n_items, ie_batch_item* items, int32_t max_conc
 /* Copy the electric field of the last source of the last ie_solve to the host ([3][nz][ny][nx]
  * complex, interleaved). IE_ESTATE if no solve has run. */
 ie_status ie_get_field(ie_ctx* ctx, double* E_out);
+
+/* Device-pointer variants (no synchronisation; complex128 [3][nz][ny][nx] on the current device):
+ * copy the field of the last solve into E_dev (IE_ESTATE if none), or write the incident field of one
+ * dipole into E0_dev. */
+ie_status ie_get_field_dev(ie_ctx* ctx, double* E_dev);
+ie_status ie_incident_field_dev(ie_ctx* ctx, const ie_dipole* src, double* E0_dev);
+
+/* Initial guess for the next ie_solve (its first source): E_dev, complex128 [3][nz][ny][nx] on the
+ * device, is copied on the context stream and replaces the initial E := E0 of Algorithm 1 if its FP64
+ * residual e (eq. 9) is smaller than that of E0; otherwise the solve starts from E0 as usual (ie_info
+ * reports both residuals and the choice). The guess is consumed by that solve. NULL clears it. */
+ie_status ie_set_initial_field_dev(ie_ctx* ctx, const double* E_dev);
 
 /* Apply the operator of one sub-domain, y = (I - G^(ii) dsigma^(i)) x (eq. 8 restricted to the slab
  * z in [z0, z0+nz), block-sized FFT convolution as used inside GMRES), on host arrays

@@ -90,6 +90,8 @@ struct ie_ctx {
 
   DevBuf E, E0, R;  // c128 whole-grid fields
   bool has_field = false;
+  DevBuf Einit;           // initial guess for the next solve (ie_set_initial_field_dev)
+  bool has_init = false;
 
   // Krylov workspace (one precision at a time; sized on demand)
   DevBuf V, kx, kb, kt1, kt2;
@@ -621,12 +623,27 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
   cudaStream_t s = c->stream;
   const long nxy = (long)c->nx * c->ny;
   const int M = (int)cfg.split.size() - 1;
+  const bool warm = c->has_init;
+  c->has_init = false;  // an initial guess serves one source
   CK(cudaMemcpyAsync(c->E.p, c->E0.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToDevice, s));
   double e0norm;
   CKS(norm_c128(c, c->E0.as<double2>(), c->N, nullptr, 0, c->N, &e0norm));
   if (e0norm == 0.0) return IE_OK;  // no incident field inside the grid: E = 0
   double e;
   CKS(full_residual(c, e0norm, &e));
+  if (warm) {  // a given initial guess replaces E := E0 only if its residual is smaller
+    const double e_cold = e;
+    CK(cudaMemcpyAsync(c->E.p, c->Einit.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToDevice, s));
+    CKS(full_residual(c, e0norm, &e));
+    info->cold_rel_residual = e_cold;
+    info->warm_rel_residual = e;
+    if (e < e_cold) {
+      info->warm_start_used = 1;
+    } else {
+      CK(cudaMemcpyAsync(c->E.p, c->E0.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToDevice, s));
+      CKS(full_residual(c, e0norm, &e));
+    }
+  }
   if (record) {
     info->n_history = 1;
     info->residual_history[0] = e;
@@ -1011,6 +1028,34 @@ ie_status ie_solve_batch(int32_t n_items, ie_batch_item* items, int32_t max_conc
   }
   for (int i = 0; i < n_items; ++i)
     if (items[i].status != IE_OK) return items[i].status;
+  return IE_OK;
+}
+
+ie_status ie_set_initial_field_dev(ie_ctx* c, const double* E_dev) {
+  if (!c) return IE_EINVAL;
+  if (!E_dev) {
+    c->has_init = false;
+    return IE_OK;
+  }
+  CK(c->Einit.ensure(sizeof(double2) * 3 * c->N));
+  CK(cudaMemcpyAsync(c->Einit.p, E_dev, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  c->has_init = true;
+  return IE_OK;
+}
+
+ie_status ie_get_field_dev(ie_ctx* c, double* E_dev) {
+  if (!c || !E_dev) return fail(c, IE_EINVAL, "null argument");
+  if (!c->has_field) return fail(c, IE_ESTATE, "no solve has run");
+  CK(cudaMemcpyAsync(E_dev, c->E.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  return IE_OK;
+}
+
+ie_status ie_incident_field_dev(ie_ctx* c, const ie_dipole* src, double* E0_dev) {
+  if (!c || !src || !E0_dev) return fail(c, IE_EINVAL, "null argument");
+  CKS(check_point(c, src->pos));
+  KL(IE_K_FIELD, 48.0 * c->N,
+     launch_incident_E(reinterpret_cast<double2*>(E0_dev), c->nx, c->ny, c->nz, c->origin, c->h, src->pos,
+                       src->moment, c->k0, c->omega * kMu0, c->stream));
   return IE_OK;
 }
 

@@ -51,7 +51,9 @@ class ie_info(ct.Structure):
     _fields_ = [("outer_iters", ct.c_int32), ("gmres_iters_total", ct.c_int32), ("matvecs", ct.c_int32),
                 ("n_history", ct.c_int32), ("final_rel_residual", ct.c_double), ("seconds", ct.c_double),
                 ("residual_history", ct.c_double * IE_MAX_HISTORY),
-                ("sweep_gmres_iters", ct.c_int32 * IE_MAX_HISTORY), ("reorth_passes", ct.c_int32)]
+                ("sweep_gmres_iters", ct.c_int32 * IE_MAX_HISTORY), ("reorth_passes", ct.c_int32),
+                ("warm_start_used", ct.c_int32), ("cold_rel_residual", ct.c_double),
+                ("warm_rel_residual", ct.c_double)]
 
     def history(self):
         return list(self.residual_history[: self.n_history])
@@ -72,6 +74,9 @@ _SIGS = {
     "ie_solve": (ct.c_int, [_P, ct.c_int32, ct.POINTER(ie_dipole), ct.c_int32, _D, ct.c_int32, ct.c_double,
                             ct.POINTER(ie_opts), _D, ct.POINTER(ie_info)]),
     "ie_get_field": (ct.c_int, [_P, _D]),
+    "ie_get_field_dev": (ct.c_int, [_P, _P]),
+    "ie_incident_field_dev": (ct.c_int, [_P, ct.POINTER(ie_dipole), _P]),
+    "ie_set_initial_field_dev": (ct.c_int, [_P, _P]),
     "ie_solve_batch": (ct.c_int, [ct.c_int32, ct.POINTER(ie_batch_item), ct.c_int32]),
     "ie_matvec": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_int32, _D, _D]),
     "ie_matvec_dev": (ct.c_int, [_P, ct.c_int32, ct.c_int32, _P, _P]),
@@ -88,6 +93,20 @@ _SIGS = {
     "ie_tuned_tiles": (ct.c_int32, [ct.c_char_p, ct.c_int32]),
     "ie_last_error": (ct.c_char_p, [_P]),
     "ie_destroy": (None, [_P]),
+    # include/ie_fno.h
+    "ie_fno_create": (ct.c_int, [ct.c_int32] * 9 + [ct.POINTER(_P)]),
+    "ie_fno_param_count": (ct.c_int64, [_P]),
+    "ie_fno_set_stream": (ct.c_int, [_P, _P]),
+    "ie_fno_set_params": (ct.c_int, [_P, ct.POINTER(ct.c_float)]),
+    "ie_fno_get_params": (ct.c_int, [_P, ct.POINTER(ct.c_float)]),
+    "ie_fno_forward": (ct.c_int, [_P, ct.c_int32, _P, _P]),
+    "ie_fno_backward": (ct.c_int, [_P, ct.c_int32, _P, _P, ct.POINTER(ct.c_float)]),
+    "ie_fno_train_step": (ct.c_int, [_P, ct.c_int32, _P, _P, ct.c_float, ct.POINTER(ct.c_float)]),
+    "ie_fno_encode": (ct.c_int, [_P, _P, ct.c_double, _P, _P, _P]),
+    "ie_fno_encode_target": (ct.c_int, [_P, _P, _P, _P, _P]),
+    "ie_fno_decode": (ct.c_int, [_P, _P, _P, _P, _P]),
+    "ie_fno_last_error": (ct.c_char_p, [_P]),
+    "ie_fno_destroy": (None, [_P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -198,6 +217,17 @@ class Context:
         self._check(_lib.ie_get_field(self.ptr, _dptr(E)))
         return E
 
+    def get_field_dev(self, E_dev):
+        self._check(_lib.ie_get_field_dev(self.ptr, _P(_addr(E_dev))))
+
+    def incident_field_dev(self, src, E0_dev):
+        d = _dipole(src)
+        self._check(_lib.ie_incident_field_dev(self.ptr, ct.byref(d), _P(_addr(E0_dev))))
+
+    def set_initial_field_dev(self, E_dev):
+        """Initial guess for the next solve (complex128 [3][nz][ny][nx] device tensor), or None."""
+        self._check(_lib.ie_set_initial_field_dev(self.ptr, _P(_addr(E_dev)) if E_dev is not None else None))
+
     def matvec(self, x: np.ndarray, z0=0, nz=None, precision=IE_PREC_MIXED) -> np.ndarray:
         nz = self.nz if nz is None else nz
         n = 3 * nz * self.ny * self.nx
@@ -307,6 +337,100 @@ def solve_batch(problems, max_concurrent=0):
         outs.append((H, info))
     _lib.ie_solve_batch(n, items, int(max_concurrent))
     return [(H, info, items[i].status) for i, (H, info) in enumerate(outs)]
+
+
+class FNO:
+    """Owns one ``ie_fno*`` (include/ie_fno.h); methods are the ABI calls of the same name.
+
+    Device arguments are torch tensors (or raw addresses) on the current device; parameters travel as
+    flat FP32 numpy vectors in the order and layout of the header."""
+
+    def __init__(self, n, modes=12, width=32, layers=4, cin=12, cout=6, hidden=128, batch_max=8, bf16=True):
+        p = _P()
+        st = _lib.ie_fno_create(int(n), int(modes), int(width), int(layers), int(cin), int(cout), int(hidden),
+                                int(batch_max), int(bool(bf16)), ct.byref(p))
+        if st != IE_OK:
+            raise IEError(st, "ie_fno_create failed")
+        self.ptr = p
+        self.n, self.modes, self.width, self.layers = int(n), int(modes), int(width), int(layers)
+        self.cin, self.cout, self.hidden, self.batch_max = int(cin), int(cout), int(hidden), int(batch_max)
+
+    def _check(self, st):
+        if st != IE_OK:
+            raise IEError(st, _lib.ie_fno_last_error(self.ptr).decode())
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            _lib.ie_fno_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def param_count(self) -> int:
+        return int(_lib.ie_fno_param_count(self.ptr))
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(_lib.ie_fno_set_stream(self.ptr, _P(handle or 0)))
+
+    def set_params(self, flat: np.ndarray):
+        v = np.ascontiguousarray(flat, dtype=np.float32)
+        if v.size != self.param_count():
+            raise ValueError(f"expected {self.param_count()} parameters, got {v.size}")
+        self._check(_lib.ie_fno_set_params(self.ptr, v.ctypes.data_as(ct.POINTER(ct.c_float))))
+
+    def get_params(self) -> np.ndarray:
+        v = np.zeros(self.param_count(), dtype=np.float32)
+        self._check(_lib.ie_fno_get_params(self.ptr, v.ctypes.data_as(ct.POINTER(ct.c_float))))
+        return v
+
+    def forward(self, batch, a_dev, u_dev):
+        self._check(_lib.ie_fno_forward(self.ptr, int(batch), _P(_addr(a_dev)), _P(_addr(u_dev))))
+
+    def backward(self, batch, a_dev, du_dev, want_host=True):
+        g = np.zeros(self.param_count(), dtype=np.float32) if want_host else None
+        self._check(_lib.ie_fno_backward(self.ptr, int(batch), _P(_addr(a_dev)), _P(_addr(du_dev)),
+                                         g.ctypes.data_as(ct.POINTER(ct.c_float)) if want_host else None))
+        return g
+
+    def train_step(self, batch, a_dev, t_dev, lr, want_loss=True):
+        loss = ct.c_float(0.0)
+        self._check(_lib.ie_fno_train_step(self.ptr, int(batch), _P(_addr(a_dev)), _P(_addr(t_dev)), float(lr),
+                                           ct.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def encode(self, sigma6_dev, sigma0, b_dev, a_dev, bnorm_dev):
+        self._check(_lib.ie_fno_encode(self.ptr, _P(_addr(sigma6_dev)), float(sigma0), _P(_addr(b_dev)),
+                                       _P(_addr(a_dev)), _P(_addr(bnorm_dev))))
+
+    def encode_target(self, E_dev, b_dev, bnorm_dev, t_dev):
+        self._check(_lib.ie_fno_encode_target(self.ptr, _P(_addr(E_dev)), _P(_addr(b_dev)), _P(_addr(bnorm_dev)),
+                                              _P(_addr(t_dev))))
+
+    def decode(self, u_dev, b_dev, bnorm_dev, x0_dev):
+        self._check(_lib.ie_fno_decode(self.ptr, _P(_addr(u_dev)), _P(_addr(b_dev)), _P(_addr(bnorm_dev)),
+                                       _P(_addr(x0_dev))))
+
+
+def fno_flat(params) -> np.ndarray:
+    """Flatten a parameter set (lists of arrays in the header's order; complex arrays interleaved)."""
+    parts = []
+    for arr in params:
+        a = np.asarray(arr)
+        if np.iscomplexobj(a):
+            a = np.stack([a.real, a.imag], axis=-1)
+        parts.append(a.astype(np.float32).ravel())
+    return np.concatenate(parts)
 
 
 def tuned_tiles() -> str:

@@ -140,13 +140,16 @@ def layered_vti(grid: Grid, seed: int, n_layers: int = 3, ratio_max: float = 5.0
 
 
 def dipping_ti_with_ellipsoids(grid: Grid, seed: int, n_layers: int = 5, ratio_max: float = 10.0,
-                               dip_max_deg: float = 30.0, n_ellipsoids: int = 2) -> np.ndarray:
-    """Dipping TI layers (common dip/azimuth, Appendix C rotation) plus isotropic ellipsoids."""
+                               dip_max_deg: float = 30.0, n_ellipsoids: int = 2, eval_grid: Grid | None = None) -> np.ndarray:
+    """Dipping TI layers (common dip/azimuth, Appendix C rotation) plus isotropic ellipsoids.
+
+    The model is drawn for ``grid``; ``eval_grid`` (default ``grid``) is where it is evaluated, so a
+    sub-grid of ``grid`` gives exactly the corresponding crop of the full model."""
     rng = np.random.default_rng(seed)
     theta = np.deg2rad(rng.uniform(0.0, dip_max_deg))
     phi = rng.uniform(0.0, 2.0 * np.pi)
     nrm = np.array([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)])
-    xc, yc, zc = grid.centres()
+    xc, yc, zc = (eval_grid or grid).centres()
     Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
     dist = X * nrm[0] + Y * nrm[1] + Z * nrm[2]
     half = 0.5 * grid.h * np.array([grid.nx, grid.ny, grid.nz])
@@ -293,6 +296,22 @@ def config3_item(seed: int, position: int, freq: float, n_positions: int = 64, s
     src, rx = coaxial_tool()
     name = f"logging window {nx}x{ny}x{nz} @0.25 m, position {position}, {freq:g} Hz"
     return Workload(name, g, 0.1, freq, s6, src, rx, z_split=split, tol=1e-6, restart=40)
+
+
+def config4_item(seed: int, n: int = 64) -> Workload:
+    """One training/evaluation sample of the learned warm start: a model of the 128x128x256 @0.25 m
+    dipping-TI-plus-ellipsoids generator (the tool at the centre of the full model, 400 kHz, sigma0
+    0.1 S/m) cropped to an n^3 block at a seeded offset, solved as one sub-domain (no receivers).
+    The tool may lie inside or outside the block; it always sits on a cell vertex."""
+    full = centred_grid(128, 128, 256, 0.25)
+    rng = np.random.default_rng([seed, 4])
+    off = (int(rng.integers(0, full.nx - n + 1)), int(rng.integers(0, full.ny - n + 1)),
+           int(rng.integers(0, full.nz - n + 1)))
+    crop = Grid(n, n, n, full.h, tuple(full.origin[k] + off[k] * full.h for k in range(3)))
+    src, _ = coaxial_tool()
+    s6 = dipping_ti_with_ellipsoids(full, seed, eval_grid=crop)
+    name = f"warm-start block {n}^3 @0.25 m cropped at cells {off} of the 128x128x256 model, 400 kHz"
+    return Workload(name, crop, 0.1, 4.0e5, s6, src, np.zeros((0, 3)), z_split=[0, n], tol=1e-6, restart=40)
 
 
 def random_contrast_sigma6(shape, seed: int, sigma0: float, spread: float = 0.5) -> np.ndarray:

@@ -6,11 +6,11 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "ie.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("ie.h", "ie_fno.h")]
 
 
 def declared_symbols():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(ie_[a-z0-9_]+)\s*\(", text)))
 
