@@ -79,6 +79,8 @@ typedef struct {
   int32_t precision;      /* ie_precision (default IE_PREC_MIXED) */
   int32_t adaptive;       /* 1: block tolerance e/10 (Algorithm 1, "-A"); 0: fixed_tol ("-F") */
   double fixed_tol;       /* block tolerance when adaptive == 0 */
+  int32_t contraction;    /* 1: each block solve runs GMRES on the contraction form (see
+                             ie_matvec_contraction); 0 (default): on the conventional operator */
 } ie_opts;
 
 #define IE_MAX_HISTORY 128
@@ -160,6 +162,15 @@ ie_status ie_solve_batch(int32_t n_items, ie_batch_item* items, int32_t max_conc
 /* Copy the electric field of the last source of the last ie_solve to the host ([3][nz][ny][nx]
  * complex, interleaved). IE_ESTATE if no solve has run. */
 ie_status ie_get_field(ie_ctx* ctx, double* E_out);
+
+/* The contraction form of one sub-domain's operator (the remedy for high contrast named at the end of
+ * Section 2.3): y = (M - G^(ii) dsigma^(i) M) x with M = 2 sigma0 (sigma + sigma0 I)^-1 per voxel, i.e.
+ * the operator of ie_matvec right-multiplied by M. M - G dsigma M = I - C r with C = I + 2 sigma0 G and
+ * r = (sigma - sigma0 I)(sigma + sigma0 I)^-1, a contraction for a positive definite sigma, so GMRES
+ * converges in fewer iterations at high contrast. A solve with ie_opts.contraction = 1 finds u with
+ * (M - G dsigma M) u = b and adds M u to the field: the residual, its norm and the stopping rule are those
+ * of the conventional system. Same arguments, layouts and precisions (MIXED, FP64) as ie_matvec. */
+ie_status ie_matvec_contraction(ie_ctx* ctx, int32_t precision, int32_t z0, int32_t nz, const double* x, double* y);
 
 /* Device-pointer variants (no synchronisation; complex128 [3][nz][ny][nx] on the current device):
  * copy the field of the last solve into E_dev (IE_ESTATE if none), or write the incident field of one

@@ -11,8 +11,10 @@ bool supported_pencil(int L);
 constexpr int kTileVariants = 2;
 
 template <typename T> struct ConvLaunch {
+  // mt != nullptr: contraction form (ds = dsigma M, mt = M); also stores w = M x at stride w_cs
   static cudaError_t p1(int L, const FieldC<T>* x, long x_cs, const FieldR<T>* ds, long d_cs, C<T>* A, long A_cs,
-                        int nx, long nrows, const C<T>* tw, cudaStream_t s);
+                        int nx, long nrows, const C<T>* tw, cudaStream_t s, const FieldR<T>* mt = nullptr,
+                        FieldC<T>* w = nullptr, long w_cs = 0);
   static cudaError_t p5(int L, int mode, const C<T>* A, long A_cs, int nx, long nrows, const FieldC<T>* xin,
                         long x_cs, FieldC<T>* y, long y_cs, double2* r, long r_cs, const double2* b, long b_cs,
                         const C<T>* tw, cudaStream_t s);

@@ -31,10 +31,13 @@ template <typename T, int L, int WDIV = 1> struct LaneCfg {
 };
 
 // ---------------------------------------------------------------- P1: J = dsigma x, x-FFT
-template <typename T, int L>
+// CONTRACT: the contraction form, where ds holds dsigma M and mt holds M (both [6][...]); the kernel
+// then also stores w = M x (the field the epilogue of P5 subtracts the convolution from).
+template <typename T, int L, bool CONTRACT>
 __global__ void __launch_bounds__(kThreads) k_p1_contrast_fftx(
     const FieldC<T>* __restrict__ x, long x_cs, const FieldR<T>* __restrict__ ds, long d_cs,
-    C<T>* __restrict__ A, long A_cs, int nx, long nrows, const C<T>* __restrict__ tw) {
+    C<T>* __restrict__ A, long A_cs, int nx, long nrows, const C<T>* __restrict__ tw,
+    const FieldR<T>* __restrict__ mt, FieldC<T>* __restrict__ w, long w_cs) {
   using R = FieldR<T>;
   constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, P = RowCfg<T, L>::P;
   __shared__ C<T> smem[P * RowSM<T>::words(L)];
@@ -54,6 +57,13 @@ __global__ void __launch_bounds__(kThreads) k_p1_contrast_fftx(
       J[0][m] = to_c(mk<R>(sxx * x0.x + sxy * x1.x + sxz * x2.x, sxx * x0.y + sxy * x1.y + sxz * x2.y), T());
       J[1][m] = to_c(mk<R>(sxy * x0.x + syy * x1.x + syz * x2.x, sxy * x0.y + syy * x1.y + syz * x2.y), T());
       J[2][m] = to_c(mk<R>(sxz * x0.x + syz * x1.x + szz * x2.x, sxz * x0.y + syz * x1.y + szz * x2.y), T());
+      if constexpr (CONTRACT) {
+        const R mxx = mt[o], myy = mt[d_cs + o], mzz = mt[2 * d_cs + o];
+        const R mxy = mt[3 * d_cs + o], mxz = mt[4 * d_cs + o], myz = mt[5 * d_cs + o];
+        w[o] = mk<R>(mxx * x0.x + mxy * x1.x + mxz * x2.x, mxx * x0.y + mxy * x1.y + mxz * x2.y);
+        w[w_cs + o] = mk<R>(mxy * x0.x + myy * x1.x + myz * x2.x, mxy * x0.y + myy * x1.y + myz * x2.y);
+        w[2 * w_cs + o] = mk<R>(mxz * x0.x + myz * x1.x + mzz * x2.x, mxz * x0.y + myz * x1.y + mzz * x2.y);
+      }
     } else {
       J[0][m] = J[1][m] = J[2][m] = czero<C<T>>();
     }

@@ -5,6 +5,8 @@
 #include "conv.cuh"
 #include "conv_kernels.cuh"
 
+#include <type_traits>
+
 namespace ie {
 
 #define IE_FOR_EACH_L(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
@@ -23,15 +25,25 @@ inline bool supported_pencil_impl(int L) {
 
 template <typename T>
 cudaError_t ConvLaunch<T>::p1(int L, const FieldC<T>* x, long x_cs, const FieldR<T>* ds, long d_cs, C<T>* A,
-                              long A_cs, int nx, long nrows, const C<T>* tw, cudaStream_t s) {
+                              long A_cs, int nx, long nrows, const C<T>* tw, cudaStream_t s, const FieldR<T>* mt,
+                              FieldC<T>* w, long w_cs) {
   if (nrows <= 0) return cudaSuccess;
+  if (mt && std::is_same<T, df>::value) return cudaErrorInvalidValue;  // contraction: float and double only
   switch (L) {
-#define IE_CASE(N)                                                                              \
-  case N: {                                                                                     \
-    constexpr int P = RowCfg<T, N>::P;                                                          \
-    dim3 blk(Plan<T, N>::TT, P), grd((unsigned)((nrows + P - 1) / P));                         \
-    k_p1_contrast_fftx<T, N><<<grd, blk, 0, s>>>(x, x_cs, ds, d_cs, A, A_cs, nx, nrows, tw);    \
-    break;                                                                                      \
+#define IE_CASE(N)                                                                                   \
+  case N: {                                                                                          \
+    constexpr int P = RowCfg<T, N>::P;                                                               \
+    dim3 blk(Plan<T, N>::TT, P), grd((unsigned)((nrows + P - 1) / P));                              \
+    if constexpr (!std::is_same<T, df>::value) {                                                     \
+      if (mt) {                                                                                      \
+        k_p1_contrast_fftx<T, N, true><<<grd, blk, 0, s>>>(x, x_cs, ds, d_cs, A, A_cs, nx, nrows, tw, mt, \
+                                                           w, w_cs);                                 \
+        break;                                                                                       \
+      }                                                                                              \
+    }                                                                                                \
+    k_p1_contrast_fftx<T, N, false><<<grd, blk, 0, s>>>(x, x_cs, ds, d_cs, A, A_cs, nx, nrows, tw, nullptr, \
+                                                        nullptr, 0);                                 \
+    break;                                                                                           \
   }
     IE_FOR_EACH_L(IE_CASE)
 #undef IE_CASE

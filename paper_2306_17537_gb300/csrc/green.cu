@@ -108,6 +108,55 @@ __global__ void k_set_contrast(const double* __restrict__ s6, long N, double sig
   }
 }
 
+// Contraction-form tensors from the contrast (both symmetric, [6][N], FP64 and FP32):
+//   M = 2 sigma0 (sigma + sigma0 I)^-1 = 2 sigma0 (dsigma + 2 sigma0 I)^-1,   K = dsigma M
+// (dsigma and M commute, so K is symmetric). The inverse is the adjugate over the determinant of the
+// positive definite sigma + sigma0 I.
+__global__ void k_contract_tensors(const double* __restrict__ d64, long N, double sigma0, double* __restrict__ K64,
+                                   double* __restrict__ M64, float* __restrict__ K32, float* __restrict__ M32) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+    const double dxx = d64[i], dyy = d64[N + i], dzz = d64[2 * N + i];
+    const double dxy = d64[3 * N + i], dxz = d64[4 * N + i], dyz = d64[5 * N + i];
+    const double axx = dxx + 2 * sigma0, ayy = dyy + 2 * sigma0, azz = dzz + 2 * sigma0;
+    const double cxx = ayy * azz - dyz * dyz, cyy = axx * azz - dxz * dxz, czz = axx * ayy - dxy * dxy;
+    const double cxy = dxz * dyz - dxy * azz, cxz = dxy * dyz - dxz * ayy, cyz = dxy * dxz - axx * dyz;
+    const double det = axx * cxx + dxy * cxy + dxz * cxz;
+    const double f = 2 * sigma0 / det;
+    const double m[6] = {f * cxx, f * cyy, f * czz, f * cxy, f * cxz, f * cyz};
+    // K = dsigma M (symmetric): rows of dsigma times columns of M
+    const double k[6] = {dxx * m[0] + dxy * m[3] + dxz * m[4], dxy * m[3] + dyy * m[1] + dyz * m[5],
+                         dxz * m[4] + dyz * m[5] + dzz * m[2], dxx * m[3] + dxy * m[1] + dxz * m[5],
+                         dxx * m[4] + dxy * m[5] + dxz * m[2], dxy * m[4] + dyy * m[5] + dyz * m[2]};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      M64[c * N + i] = m[c];
+      K64[c * N + i] = k[c];
+      M32[c * N + i] = (float)m[c];
+      K32[c * N + i] = (float)k[c];
+    }
+  }
+}
+
+// x := M x in place for a symmetric [6][...] tensor (block-local vectors, component stride cs).
+template <typename V, typename R>
+__global__ void k_apply_sym6(const R* __restrict__ M, long m_cs, V* __restrict__ x, long cs, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const R mxx = M[i], myy = M[m_cs + i], mzz = M[2 * m_cs + i], mxy = M[3 * m_cs + i], mxz = M[4 * m_cs + i],
+            myz = M[5 * m_cs + i];
+    const V a = x[i], b = x[cs + i], c = x[2 * cs + i];
+    V o0, o1, o2;
+    o0.x = mxx * a.x + mxy * b.x + mxz * c.x;
+    o0.y = mxx * a.y + mxy * b.y + mxz * c.y;
+    o1.x = mxy * a.x + myy * b.x + myz * c.x;
+    o1.y = mxy * a.y + myy * b.y + myz * c.y;
+    o2.x = mxz * a.x + myz * b.x + mzz * c.x;
+    o2.y = mxz * a.y + myz * b.y + mzz * c.y;
+    x[i] = o0;
+    x[cs + i] = o1;
+    x[2 * cs + i] = o2;
+  }
+}
+
 // Incident field E0 = i omega mu0 grad g(r - r_s) x m at every cell centre, c128 [3][N].
 __global__ void k_incident_E(double2* __restrict__ E0, int nx, int ny, int nz, double ox, double oy, double oz,
                              double h, double sx, double sy, double sz, double mx, double my, double mz, double2 k,
@@ -240,6 +289,20 @@ cudaError_t launch_extract_octant(const double2* full, int Lx, int Ly, int Lz, d
 cudaError_t launch_set_contrast(const double* s6, long N, double sigma0, double* d64, float* d32, int* bad,
                                 cudaStream_t s) {
   k_set_contrast<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(s6, N, sigma0, d64, d32, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_tensors(const double* d64, long N, double sigma0, double* K64, double* M64, float* K32,
+                                    float* M32, cudaStream_t s) {
+  k_contract_tensors<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(d64, N, sigma0, K64, M64, K32, M32);
+  return cudaGetLastError();
+}
+cudaError_t launch_apply_sym6(const float* M, long m_cs, float2* x, long cs, long n, cudaStream_t s) {
+  k_apply_sym6<float2, float><<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(M, m_cs, x, cs, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_apply_sym6(const double* M, long m_cs, double2* x, long cs, long n, cudaStream_t s) {
+  k_apply_sym6<double2, double><<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(M, m_cs, x, cs, n);
   return cudaGetLastError();
 }
 

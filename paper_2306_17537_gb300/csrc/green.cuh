@@ -12,6 +12,12 @@ cudaError_t launch_green_tab(double2* out, int comp, int Lx, int Ly, int Lz, int
 // octant of the scaled spectrum in complex128, complex64 and double-float (odf: [n] x 16 bytes)
 cudaError_t launch_extract_octant(const double2* full, int Lx, int Ly, int Lz, double scale, double2* o64,
                                   float2* o32, void* odf, cudaStream_t s);
+// Contraction form: M = 2 sigma0 (dsigma + 2 sigma0 I)^-1 and K = dsigma M from the FP64 contrast.
+cudaError_t launch_contract_tensors(const double* d64, long N, double sigma0, double* K64, double* M64, float* K32,
+                                    float* M32, cudaStream_t s);
+// x := M x in place (M symmetric [6][...] at stride m_cs; x [3][n] at stride cs).
+cudaError_t launch_apply_sym6(const float* M, long m_cs, float2* x, long cs, long n, cudaStream_t s);
+cudaError_t launch_apply_sym6(const double* M, long m_cs, double2* x, long cs, long n, cudaStream_t s);
 cudaError_t launch_set_contrast(const double* s6, long N, double sigma0, double* d64, float* d32, int* bad,
                                 cudaStream_t s);
 cudaError_t launch_incident_E(double2* E0, int nx, int ny, int nz, const double* origin, double h, const double* pos,

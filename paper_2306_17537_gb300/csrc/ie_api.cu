@@ -82,6 +82,9 @@ struct ie_ctx {
 
   DevBuf tw64, tw32, twdf;
   DevBuf ds64, ds32, s6_stage;
+  DevBuf ck64, cm64, ck32, cm32;  // contraction form: K = dsigma M and M (built on first use)
+  bool contract_ready = false;
+  DevBuf cw32, cw64;             // w = M x of the contraction operator (block-local scratch)
   bool has_contrast = false;
   std::vector<SpecSet*> specs;
 
@@ -322,10 +325,19 @@ template <class F> cudaError_t tune(ie_ctx* c, const TuneKey& k, F&& run, int* b
 // One FFT convolution G^(ts) dsigma^(s) x with the given spectra and epilogue (see conv_kernels.cuh).
 //   x: source field, components at stride x_cs, covering the slab [zs0, zs0 + nzs) of the grid;
 //   os/ot: pencil positions of the source / target slab inside the padded z axis of `S`.
+// Contraction form of P1 (see k_p1_contrast_fftx): K = dsigma M and M on the whole grid, w the
+// block-local destination of M x.
+template <typename T> struct Contract {
+  const FieldR<T>* K;
+  const FieldR<T>* M;
+  FieldC<T>* w;
+  long w_cs;
+};
+
 template <typename T>
 ie_status conv(ie_ctx* c, const SpecSet* S, const FieldC<T>* x, long x_cs, int zs0, int nzs, int os, int nzt, int ot,
                int mode, const FieldC<T>* xin, long xin_cs, FieldC<T>* y, long y_cs, double2* r, long r_cs,
-               const double2* b, long b_cs) {
+               const double2* b, long b_cs, const Contract<T>* ca = nullptr) {
   CKS(ensure_conv_ws<T>(c, std::max(nzs, nzt)));
   const long zc = std::is_same<T, float>::value ? c->zcap32 : c->zcap64;
   C<T>* A = (std::is_same<T, float>::value ? c->A32 : c->A64).template as<C<T>>();
@@ -343,6 +355,9 @@ ie_status conv(ie_ctx* c, const SpecSet* S, const FieldC<T>* x, long x_cs, int z
   const TuneKey k2{2, bz, c->Ly, c->Lx, c->ny, nzs, 0}, k3{3, bz, S->Lz, c->Lx, c->Ly, nzs, nzt},
       k4{4, bz, c->Ly, c->Lx, c->ny, nzt, 0};
   auto p1 = [&]() {
+    if (ca)
+      return ConvLaunch<T>::p1(c->Lx, x, x_cs, ca->K + (long)zs0 * nxy, c->N, A, A_cs, c->nx, (long)nzs * c->ny, tw, s,
+                               ca->M + (long)zs0 * nxy, ca->w, ca->w_cs);
     return ConvLaunch<T>::p1(c->Lx, x, x_cs, dsig<T>(c) + (long)zs0 * nxy, c->N, A, A_cs, c->nx, (long)nzs * c->ny, tw,
                              s);
   };
@@ -357,7 +372,7 @@ ie_status conv(ie_ctx* c, const SpecSet* S, const FieldC<T>* x, long x_cs, int z
     return ConvLaunch<T>::lanes(c->Ly, +1, v, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx,
                                 c->Lx, c->ny, c->Lx, nzt, 3, tw, s);
   };
-  KL(k0 + 0, (3 * fz + 6 * rz) * nzs * nxy + 3 * sz * nzs * c->ny * c->Lx, p1());
+  KL(k0 + 0, (3 * fz + 6 * rz + (ca ? 6 * rz + 3 * fz : 0.0)) * nzs * nxy + 3 * sz * nzs * c->ny * c->Lx, p1());
   int v2 = tuned_variant(k2), v3 = tuned_variant(k3), v4 = tuned_variant(k4);
   if (v2 < 0) CK(tune(c, k2, p2, &v2));
   KL(k0 + 1, 3 * sz * nzs * c->Lx * (double)(c->ny + c->Ly), p2(v2));
@@ -375,22 +390,63 @@ ie_status conv(ie_ctx* c, const SpecSet* S, const FieldC<T>* x, long x_cs, int z
 }
 
 // Operator of one sub-domain, y = (I - G^(ii) dsigma^(i)) x, on block-local vectors.
+template <typename T> const FieldR<T>* ctens(const ie_ctx* c, bool k);
+template <> const float* ctens<float>(const ie_ctx* c, bool k) { return (k ? c->ck32 : c->cm32).as<float>(); }
+template <> const double* ctens<double>(const ie_ctx* c, bool k) { return (k ? c->ck64 : c->cm64).as<double>(); }
+template <> const double* ctens<df>(const ie_ctx*, bool) { return nullptr; }
+
+// Tensors of the contraction form for the current contrast (built once per ie_set_contrast).
+ie_status ensure_contract(ie_ctx* c) {
+  if (c->contract_ready) return IE_OK;
+  CK(c->ck64.ensure(sizeof(double) * 6 * c->N));
+  CK(c->cm64.ensure(sizeof(double) * 6 * c->N));
+  CK(c->ck32.ensure(sizeof(float) * 6 * c->N));
+  CK(c->cm32.ensure(sizeof(float) * 6 * c->N));
+  KL(IE_K_FIELD, 144.0 * c->N,
+     launch_contract_tensors(c->ds64.as<double>(), c->N, c->sigma0, c->ck64.as<double>(), c->cm64.as<double>(),
+                             c->ck32.as<float>(), c->cm32.as<float>(), c->stream));
+  c->contract_ready = true;
+  return IE_OK;
+}
+
+// Operator of one sub-domain on block-local vectors: y = (I - G^(ii) dsigma^(i)) x (eq. 8 restricted to
+// the slab), or with `contract` the contraction form y = (M - G^(ii) dsigma^(i) M) x, the same operator
+// right-multiplied by M = 2 sigma0 (sigma + sigma0 I)^-1 (apply_conv always gives the first).
 template <typename T> struct BlockOp {
   ie_ctx* c;
   int z0, nz;
   const SpecSet* S;
+  bool contract = false;
   long nb() const { return (long)nz * c->ny * c->nx; }
-  ie_status apply(const FieldC<T>* x, FieldC<T>* y) const {
+  ie_status apply_conv(const FieldC<T>* x, FieldC<T>* y) const {
     return conv<T>(c, S, x, nb(), z0, nz, 0, nz, 0, EPI_APPLY, x, nb(), y, nb(), nullptr, 0, nullptr, 0);
+  }
+  ie_status apply(const FieldC<T>* x, FieldC<T>* y) const {
+    if (!contract) return apply_conv(x, y);
+    DevBuf& wb = std::is_same<T, float>::value ? c->cw32 : c->cw64;
+    CK(wb.ensure(sizeof(FieldC<T>) * 3 * nb()));
+    FieldC<T>* w = wb.template as<FieldC<T>>();
+    const Contract<T> ca{ctens<T>(c, true), ctens<T>(c, false), w, nb()};
+    return conv<T>(c, S, x, nb(), z0, nz, 0, nz, 0, EPI_APPLY, w, nb(), y, nb(), nullptr, 0, nullptr, 0, &ca);
+  }
+  // x := M x (turns the contraction-form solution into the field correction)
+  ie_status to_field(FieldC<T>* x) const {
+    if (!contract) return IE_OK;
+    const long nxy = (long)c->nx * c->ny;
+    KL(IE_K_FIELD, (6.0 * sizeof(FieldR<T>) + 6.0 * sizeof(FieldC<T>)) * nb(),
+       launch_apply_sym6(ctens<T>(c, false) + (long)z0 * nxy, c->N, x, nb(), nb(), c->stream));
+    return IE_OK;
   }
 };
 
-template <typename T> ie_status make_block(ie_ctx* c, int z0, int nz, BlockOp<T>* op) {
+template <typename T> ie_status make_block(ie_ctx* c, int z0, int nz, BlockOp<T>* op, bool contract = false) {
   if (z0 < 0 || nz < 1 || z0 + nz > c->nz) return fail(c, IE_EINVAL, "slab outside the grid");
   if (!c->has_contrast) return fail(c, IE_ESTATE, "no contrast set");
+  if (contract && std::is_same<T, df>::value) return fail(c, IE_EINVAL, "contraction form: complex64 or complex128");
   SpecSet* S = nullptr;
   CKS(get_spec(c, nz, &S));
-  *op = BlockOp<T>{c, z0, nz, S};
+  if (contract) CKS(ensure_contract(c));
+  *op = BlockOp<T>{c, z0, nz, S, contract};
   return IE_OK;
 }
 
@@ -613,7 +669,7 @@ ie_status full_residual(ie_ctx* c, double e0norm, double* e) {
 struct SolveCfg {
   int dd_mode;
   std::vector<int> split;
-  int restart, max_outer, max_inner, precision, adaptive;
+  int restart, max_outer, max_inner, precision, adaptive, contraction;
   double fixed_tol, tol;
 };
 
@@ -651,7 +707,7 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
   std::vector<BlockOp<T>> ops(M);
   long nbmax = 0;
   for (int i = 0; i < M; ++i) {
-    CKS(make_block<T>(c, cfg.split[i], cfg.split[i + 1] - cfg.split[i], &ops[i]));
+    CKS(make_block<T>(c, cfg.split[i], cfg.split[i + 1] - cfg.split[i], &ops[i], cfg.contraction != 0));
     nbmax = std::max(nbmax, ops[i].nb());
   }
   SpecSet* Sfull = nullptr;
@@ -681,11 +737,11 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
       } else {
         if (std::is_same<T, float>::value) {
           KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(Ei, c->N, reinterpret_cast<float2*>(dx), nb, nb, s));
-          CKS(A.apply(dx, t2));
+          CKS(A.apply_conv(dx, t2));
           CKS(norm_c128(c, Ri, c->N, reinterpret_cast<const float2*>(t2), nb, nb, &bnorm));
         } else {
           KL(IE_K_FIELD, 96.0 * nb, launch_copy_c128(Ei, c->N, reinterpret_cast<double2*>(dx), nb, nb, s));
-          CKS(A.apply(dx, t2));
+          CKS(A.apply_conv(dx, t2));
           KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(Ri, c->N, reinterpret_cast<double2*>(t2), nb, nb, s));
           CKS(norm_c128(c, reinterpret_cast<const double2*>(t2), nb, nullptr, 0, nb, &bnorm));
         }
@@ -700,6 +756,7 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
         KL(IE_K_FIELD, 96.0 * nb, launch_copy_c128(Ri, c->N, reinterpret_cast<double2*>(rhs), nb, nb, s));
       GmresOut go;
       CKS(gmres<T>(c, A, rhs, dx, true, tol_i, cfg.restart, cfg.max_inner, &go));
+      CKS(A.to_field(dx));  // contraction form: the field correction is M times the GMRES solution
       inner_ok = inner_ok && go.converged;
       sweep_its += go.iters;
       info->gmres_iters_total += go.iters;
@@ -877,6 +934,7 @@ static ie_status set_contrast_dev_impl(ie_ctx* c, const double* s6_dev) {
   }
   c->has_contrast = true;
   c->has_field = false;
+  c->contract_ready = false;
   return IE_OK;
 }
 
@@ -914,6 +972,8 @@ ie_status ie_solve(ie_ctx* c, int32_t n_src, const ie_dipole* src, int32_t n_rx,
   cfg.adaptive = o.adaptive;
   cfg.fixed_tol = o.fixed_tol > 0 ? o.fixed_tol : tol;
   cfg.tol = tol;
+  cfg.contraction = o.contraction;
+  if (o.contraction != 0 && o.contraction != 1) return fail(c, IE_EINVAL, "contraction must be 0 or 1");
   if (cfg.precision != IE_PREC_MIXED && cfg.precision != IE_PREC_FP64) return fail(c, IE_EINVAL, "bad precision");
   const int M = (dd_mode == IE_DD_NONE) ? 1 : std::max(1, o.n_blocks);
   if (M > c->nz) return fail(c, IE_EINVAL, "more blocks than z cells");
@@ -1096,6 +1156,33 @@ ie_status ie_matvec(ie_ctx* c, int32_t precision, int32_t z0, int32_t nz, const 
     KL(IE_K_FIELD, 120.0 * nb, launch_add_c64_to_c128(ys.as<float2>(), nb, yd.as<double2>(), nb, nb, c->stream));
     CK(cudaMemcpyAsync(y, yd.p, sizeof(double2) * 3 * nb, cudaMemcpyDeviceToHost, c->stream));
   }
+  CK(sync(c));
+  return IE_OK;
+}
+
+ie_status ie_matvec_contraction(ie_ctx* c, int32_t precision, int32_t z0, int32_t nz, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, IE_EINVAL, "null argument");
+  if (precision != IE_PREC_MIXED && precision != IE_PREC_FP64) return fail(c, IE_EINVAL, "bad precision");
+  const long nb = (long)nz * c->ny * c->nx;
+  DevBuf xd, yd, xs, ys;
+  CKS(upload_c128(c, x, 3 * std::max(nb, 0L), xd));
+  if (precision == IE_PREC_FP64) {
+    BlockOp<double> A;
+    CKS(make_block<double>(c, z0, nz, &A, true));
+    CK(yd.ensure(sizeof(double2) * 3 * nb));
+    CKS(A.apply(xd.as<double2>(), yd.as<double2>()));
+  } else {
+    BlockOp<float> A;
+    CKS(make_block<float>(c, z0, nz, &A, true));
+    CK(xs.ensure(sizeof(float2) * 3 * nb));
+    CK(ys.ensure(sizeof(float2) * 3 * nb));
+    CK(yd.ensure(sizeof(double2) * 3 * nb));
+    KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(xd.as<double2>(), nb, xs.as<float2>(), nb, nb, c->stream));
+    CKS(A.apply(xs.as<float2>(), ys.as<float2>()));
+    CK(cudaMemsetAsync(yd.p, 0, sizeof(double2) * 3 * nb, c->stream));
+    KL(IE_K_FIELD, 120.0 * nb, launch_add_c64_to_c128(ys.as<float2>(), nb, yd.as<double2>(), nb, nb, c->stream));
+  }
+  CK(cudaMemcpyAsync(y, yd.p, sizeof(double2) * 3 * nb, cudaMemcpyDeviceToHost, c->stream));
   CK(sync(c));
   return IE_OK;
 }

@@ -37,7 +37,7 @@ class ie_dipole(ct.Structure):
 class ie_opts(ct.Structure):
     _fields_ = [("n_blocks", ct.c_int32), ("z_split", ct.POINTER(ct.c_int32)), ("restart", ct.c_int32),
                 ("max_outer", ct.c_int32), ("max_inner", ct.c_int32), ("precision", ct.c_int32),
-                ("adaptive", ct.c_int32), ("fixed_tol", ct.c_double)]
+                ("adaptive", ct.c_int32), ("fixed_tol", ct.c_double), ("contraction", ct.c_int32)]
 
 
 class ie_batch_item(ct.Structure):
@@ -80,6 +80,7 @@ _SIGS = {
     "ie_solve_batch": (ct.c_int, [ct.c_int32, ct.POINTER(ie_batch_item), ct.c_int32]),
     "ie_matvec": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_int32, _D, _D]),
     "ie_matvec_dev": (ct.c_int, [_P, ct.c_int32, ct.c_int32, _P, _P]),
+    "ie_matvec_contraction": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_int32, _D, _D]),
     "ie_matvec_dev_noalloc": (ct.c_int, [_P, ct.c_int32, ct.c_int32, _P, _P]),
     "ie_interaction": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, _D, _D]),
     "ie_gmres": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_int32, _D, _D, ct.c_double, ct.c_int32, ct.c_int32, _D,
@@ -234,6 +235,15 @@ class Context:
         xx = _c128(x, n)
         y = np.zeros(n, dtype=np.complex128)
         self._check(_lib.ie_matvec(self.ptr, int(precision), int(z0), int(nz), _dptr(xx), _dptr(y)))
+        return y.reshape(3, nz, self.ny, self.nx)
+
+    def matvec_contraction(self, x: np.ndarray, z0=0, nz=None, precision=IE_PREC_MIXED) -> np.ndarray:
+        """y = (M - G dsigma M) x on the slab (ie_matvec_contraction)."""
+        nz = self.nz if nz is None else nz
+        n = 3 * nz * self.ny * self.nx
+        xx = _c128(x, n)
+        y = np.zeros(n, dtype=np.complex128)
+        self._check(_lib.ie_matvec_contraction(self.ptr, int(precision), int(z0), int(nz), _dptr(xx), _dptr(y)))
         return y.reshape(3, nz, self.ny, self.nx)
 
     def matvec_dev(self, x_dev, y_dev, z0=0, nz=None):
@@ -442,7 +452,7 @@ def tuned_tiles() -> str:
 
 
 def make_opts(n_blocks=1, z_split=None, restart=30, max_outer=50, max_inner=600, precision=IE_PREC_MIXED,
-              adaptive=True, fixed_tol=1e-6) -> ie_opts:
+              adaptive=True, fixed_tol=1e-6, contraction=False) -> ie_opts:
     o = ie_default_opts()
     o.n_blocks = int(n_blocks)
     if z_split is not None:
@@ -452,6 +462,7 @@ def make_opts(n_blocks=1, z_split=None, restart=30, max_outer=50, max_inner=600,
         o.n_blocks = len(z_split) - 1
     o.restart, o.max_outer, o.max_inner = int(restart), int(max_outer), int(max_inner)
     o.precision, o.adaptive, o.fixed_tol = int(precision), int(bool(adaptive)), float(fixed_tol)
+    o.contraction = int(bool(contraction))
     return o
 
 
