@@ -81,6 +81,10 @@ typedef struct {
   double fixed_tol;       /* block tolerance when adaptive == 0 */
   int32_t contraction;    /* 1: each block solve runs GMRES on the contraction form (see
                              ie_matvec_contraction); 0 (default): on the conventional operator */
+  int32_t graph;          /* 1: each block solve is one CUDA graph (Givens rotations, stopping test
+                             and restarts on the device, one host synchronisation per block solve;
+                             per-kernel timing of ie_profile_enable then covers only the launches
+                             outside the graph); 0 (default): host-driven Arnoldi loop */
 } ie_opts;
 
 #define IE_MAX_HISTORY 128

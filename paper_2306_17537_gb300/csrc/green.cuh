@@ -1,6 +1,7 @@
 // Declarations of the FP64 setup / receiver launchers (green.cu) and the Krylov vector launchers
 // (krylov.cu).
 #pragma once
+#include <cstddef>
 #include "common.cuh"
 
 namespace ie {
@@ -50,8 +51,9 @@ template <typename T> struct Krylov {
   static cudaError_t update(const C<T>* V, long ld, int nv, const double2* h, C<T>* w, long n, double2* out_norm,
                             const double2* ref, double eta2, int* flag, const int* skip, const RedScratch& sc,
                             cudaStream_t s);
-  // x += sum_k y_k V_k
-  static cudaError_t combine(const C<T>* V, long ld, int nv, const double2* y, C<T>* x, long n, cudaStream_t s);
+  // x += sum_k y_k V_k (k < nv, or k < *nv_dev when nv_dev is not null; nv is then the upper bound)
+  static cudaError_t combine(const C<T>* V, long ld, int nv, const double2* y, C<T>* x, long n, cudaStream_t s,
+                             const int* nv_dev = nullptr);
   // dst = src / sqrt(nrm2->x) (0 if the norm is 0), or dst = src * host_scale when nrm2 is null
   static cudaError_t scale(const C<T>* src, C<T>* dst, long n, const double2* nrm2, double host_scale, cudaStream_t s);
   // *out = |v|^2
@@ -60,6 +62,49 @@ template <typename T> struct Krylov {
   static cudaError_t rsub(const C<T>* b, C<T>* y, long n, double2* out, const RedScratch& sc, cudaStream_t s);
 };
 int krylov_blocks(long n);
+
+// ---------------------------------------------------------------- GMRES driven from the device
+// State of one restarted GMRES solve whose Givens rotations, stopping tests and restarts run on the
+// device (one CUDA graph per solve; see gm_* launchers). FP64 throughout.
+constexpr int kGmMaxM = 128;     // restart length limit (the host path allows 127)
+constexpr int kGmMaxCycles = 512;  // restart cycles whose lengths are recorded for the accounting
+struct GmState {
+  int j;        // Arnoldi steps done in the current cycle
+  int iters;    // Arnoldi steps in total
+  int cycles;   // restart cycles finished
+  int status;   // 0 running, 1 converged, 2 iteration limit or breakdown with residual > tol, 3 non-finite
+  int jd;       // steps of the cycle being combined (back-substitution length)
+  int reorth;   // Arnoldi steps that took the second Gram-Schmidt pass
+  int max_it, m;
+  double tol, bnorm, beta, rel, est, spare;
+  double2 cs[kGmMaxM], sn[kGmMaxM], g[kGmMaxM + 1], y[kGmMaxM];
+  double2 H[(kGmMaxM + 1) * kGmMaxM];  // rotated Hessenberg, (i, j) at i * kGmMaxM + j
+  int cyc_len[kGmMaxCycles];
+};
+// The scalar head of GmState, as read back by the host.
+struct GmHead {
+  int j, iters, cycles, status, jd, reorth, max_it, m;
+  double tol, bnorm, beta, rel, est, spare;
+};
+static_assert(sizeof(GmHead) == offsetof(GmState, cs), "GmHead must mirror the head of GmState");
+// bnorm from nrm2 (|b|^2); opens the solve (outer condition = bnorm > 0)
+cudaError_t gm_init(GmState* st, const double2* nrm2, cudaGraphConditionalHandle outer, cudaStream_t s);
+// Conditions of the m Arnoldi-step IF nodes of one cycle (a handle serves exactly one node).
+struct GmSteps {
+  cudaGraphConditionalHandle h[kGmMaxM];
+  int m;
+};
+// starts a restart cycle: j = 0, g = (beta, 0, ...); step 0 enabled, steps 1..m-1 disabled
+cudaError_t gm_cycle(GmState* st, const GmSteps& steps, cudaStream_t s);
+// Arnoldi step j: Hessenberg column from h[0..j] and |w|^2 (nrm2), rotations, residual estimate;
+// enables step j+1 (next, if j+1 < m) unless the estimate meets tol, the step broke down or the
+// iteration limit is reached
+cudaError_t gm_step(GmState* st, int j, const double2* h, const double2* nrm2, const int* reorth_flag,
+                    cudaGraphConditionalHandle next, bool has_next, cudaStream_t s);
+// back substitution of the current cycle into y (written as double2 to y_out) and st->jd
+cudaError_t gm_solve(GmState* st, double2* y_out, cudaStream_t s);
+// true residual |b - A x|^2 in nrm2: convergence / limit test, outer condition
+cudaError_t gm_restart(GmState* st, const double2* nrm2, cudaGraphConditionalHandle outer, cudaStream_t s);
 
 // c128 <-> c64 helpers on strided 3-component fields (slab of a whole-domain field)
 cudaError_t launch_c128_to_c64(const double2* src, long src_cs, float2* dst, long dst_cs, long n, cudaStream_t s);

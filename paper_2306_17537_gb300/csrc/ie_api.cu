@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -66,6 +67,23 @@ struct SpecSet {
   DevBuf G64, G32, Gdf;  // octants, 6 components: complex128, complex64, double-float
 };
 
+// Launches recorded while a CUDA graph is captured: (kernel class, algorithmic bytes) per launch, so
+// the accounting can be replayed for the steps the graph actually ran.
+using Tape = std::vector<std::pair<int, double>>;
+
+// One instantiated GMRES graph (see gmres_graph) and everything its kernel arguments point at.
+struct GmGraph {
+  std::vector<const void*> key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  Tape pre, head, tail;
+  std::vector<Tape> step;
+  ~GmGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
 }  // namespace ie
 
 using namespace ie;
@@ -85,6 +103,11 @@ struct ie_ctx {
   DevBuf ck64, cm64, ck32, cm32;  // contraction form: K = dsigma M and M (built on first use)
   bool contract_ready = false;
   DevBuf cw32, cw64;             // w = M x of the contraction operator (block-local scratch)
+  // GMRES as CUDA graphs: capture streams, device state, instantiated graphs (most recent last)
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
+  DevBuf gm_state;
+  std::vector<GmGraph*> gm_graphs;
+  Tape* tape = nullptr;  // non-null while a graph is being captured
   bool has_contrast = false;
   std::vector<SpecSet*> specs;
 
@@ -111,6 +134,9 @@ struct ie_ctx {
   } prof;
 
   ~ie_ctx() {
+    for (auto* g : gm_graphs) delete g;
+    for (auto st : cap)
+      if (st) cudaStreamDestroy(st);
     for (auto* s : specs) delete s;
     if (hpin) cudaFreeHost(hpin);
     for (auto e : prof.ev) cudaEventDestroy(e);
@@ -141,6 +167,10 @@ ie_status fail(ie_ctx* c, ie_status st, const std::string& msg) {
 // Launch with accounting: counts the launch and its algorithmic bytes in class `cls` and, when timing
 // is on, brackets it with a pair of CUDA events on the context stream.
 template <class F> cudaError_t kl(ie_ctx* c, int cls, double bytes, F&& f) {
+  if (c->tape) {  // inside a graph capture: record, count later per executed step
+    c->tape->emplace_back(cls, bytes);
+    return f();
+  }
   auto& P = c->prof;
   P.launches[cls]++;
   P.bytes[cls] += bytes;
@@ -666,10 +696,237 @@ ie_status full_residual(ie_ctx* c, double e0norm, double* e) {
   return IE_OK;
 }
 
+// ---------------------------------------------------------------- GMRES as one CUDA graph
+// gmres<T> with x0 = 0, with the Givens rotations, the stopping tests and the restart decision on the
+// device (krylov.cu, k_gm_*). A conditional WHILE node runs restart cycles; inside it m conditional IF
+// nodes run the Arnoldi steps j = 0..m-1 (each step enables the next one unless it met the tolerance,
+// broke down or reached the iteration limit, so the later steps are skipped), followed by the
+// back substitution, x += V y, the true residual b - A x and the restart test. A block solve is one
+// graph launch and one host synchronisation instead of one synchronisation per Arnoldi step. Every
+// wait is bounded: each cycle runs at most m steps, and the WHILE condition is cleared once the
+// iterations or the cycles reach max_it. Graphs are cached per block shape, restart length and the
+// buffers their kernels address.
+constexpr int kGmGraphCache = 8;
+
+void account(ie_ctx* c, const Tape& t) {
+  for (const auto& e : t) {
+    c->prof.launches[e.first]++;
+    c->prof.bytes[e.first] += e.second;
+  }
+}
+
+ie_status cap_stream(ie_ctx* c, int k) {
+  if (!c->cap[k]) CK(cudaStreamCreateWithFlags(&c->cap[k], cudaStreamNonBlocking));
+  return IE_OK;
+}
+
+// Adds a conditional node after the current capture point of `st` and returns its body graph.
+ie_status add_conditional(ie_ctx* c, cudaStream_t st, cudaGraphConditionalHandle h,
+                          cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return fail(c, IE_ECUDA, "graph capture is not active");
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = type;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  const cudaError_t e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm);
+  if (e != cudaSuccess)
+    return fail(c, IE_ECUDA, std::string("adding a conditional ") + (type == cudaGraphCondTypeWhile ? "WHILE" : "IF") +
+                                 " node: " + cudaGetErrorString(e));
+  CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  *body = prm.conditional.phGraph_out[0];
+  return IE_OK;
+}
+
+// Ends every capture still open on the context's capture streams (after a failed build).
+void abandon_capture(ie_ctx* c) {
+  for (int k = 2; k >= 0; --k) {
+    if (!c->cap[k]) continue;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->cap[k], &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(c->cap[k], &g);
+      if (k == 0 && g) cudaGraphDestroy(g);  // the bodies belong to their conditional nodes
+    }
+  }
+  cudaGetLastError();
+}
+
+template <typename T>
+ie_status build_gmres_graph(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, int m, bool cgs2, long n,
+                            long ld, GmGraph* G) {
+  C<T>* V = c->V.as<C<T>>();
+  C<T>* tmp = c->kt1.as<C<T>>();
+  GmState* st = c->gm_state.as<GmState>();
+  double2* dh = c->dh.as<double2>();
+  double2* dh2 = c->dh2.as<double2>();
+  double2* dn = c->dnrm.as<double2>();
+  double2* dy = c->dy.as<double2>();
+  int* flag = c->flag.as<int>();
+  const RedScratch sc = scratch(c);
+  const double sz = sizeof(C<T>);
+  c->stream = c->cap[0];
+  CK(cudaStreamBeginCapture(c->cap[0], cudaStreamCaptureModeThreadLocal));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g0 = nullptr;
+  CK(cudaStreamGetCaptureInfo(c->cap[0], &cs, nullptr, &g0, nullptr, nullptr, nullptr));
+  // a handle serves one conditional node and belongs to the graph that holds it: the WHILE node sits
+  // in the top graph, the m IF nodes (one handle each) in the WHILE body
+  cudaGraphConditionalHandle h_outer;
+  CK(cudaGraphConditionalHandleCreate(&h_outer, g0, 0, 0));
+  c->tape = &G->pre;
+  KL(IE_K_KRYLOV_MISC, sz * n, Krylov<T>::norm2(b, n, dn, sc, c->stream));
+  KL(IE_K_KRYLOV_MISC, 0, gm_init(st, dn, h_outer, c->stream));
+  CK(cudaMemsetAsync(x, 0, sizeof(C<T>) * n, c->stream));
+  KL(IE_K_KRYLOV_MISC, 2 * sz * n, Krylov<T>::scale(b, V, n, dn, 0.0, c->stream));
+  cudaGraph_t wbody = nullptr;
+  CKS(add_conditional(c, c->cap[0], h_outer, cudaGraphCondTypeWhile, &wbody));
+  GmSteps steps;
+  steps.m = m;
+  for (int j = 0; j < m; ++j) CK(cudaGraphConditionalHandleCreate(&steps.h[j], wbody, 0, 0));
+  CK(cudaStreamBeginCaptureToGraph(c->cap[1], wbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  c->stream = c->cap[1];
+  c->tape = &G->head;
+  KL(IE_K_KRYLOV_MISC, 0, gm_cycle(st, steps, c->stream));
+  G->step.assign(m, Tape());
+  for (int j = 0; j < m; ++j) {
+    cudaGraph_t ibody = nullptr;
+    CKS(add_conditional(c, c->cap[1], steps.h[j], cudaGraphCondTypeIf, &ibody));
+    CK(cudaStreamBeginCaptureToGraph(c->cap[2], ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c->stream = c->cap[2];
+    c->tape = &G->step[j];
+    C<T>* w = V + (size_t)(j + 1) * ld;
+    CKS(A.apply(V + (size_t)j * ld, w));
+    const int nv = j + 1;
+    const double ng = (nv + kDotGroup - 1) / kDotGroup;
+    KL(IE_K_DOTS, sz * n * (nv + ng), Krylov<T>::dots(V, ld, nv, w, n, cgs2, dh, nullptr, nullptr, sc, c->stream));
+    KL(IE_K_UPDATE, sz * n * (nv + 2),
+       Krylov<T>::update(V, ld, nv, dh, w, n, dn, dh + nv, 0.5, cgs2 ? flag : nullptr, nullptr, sc, c->stream));
+    if (cgs2) {
+      KL(IE_K_DOTS, 0, Krylov<T>::dots(V, ld, nv, w, n, false, dh2, dh, flag, sc, c->stream));
+      KL(IE_K_UPDATE, 0, Krylov<T>::update(V, ld, nv, dh2, w, n, dn, nullptr, 0.0, nullptr, flag, sc, c->stream));
+    }
+    KL(IE_K_KRYLOV_MISC, 2 * sz * n, Krylov<T>::scale(w, w, n, dn, 0.0, c->stream));
+    KL(IE_K_KRYLOV_MISC, 0,
+       gm_step(st, j, dh, dn, cgs2 ? flag : nullptr, steps.h[j + 1 < m ? j + 1 : j], j + 1 < m, c->stream));
+    cudaGraph_t done = nullptr;
+    CK(cudaStreamEndCapture(c->cap[2], &done));
+    c->stream = c->cap[1];
+  }
+  c->tape = &G->tail;
+  KL(IE_K_KRYLOV_MISC, 0, gm_solve(st, dy, c->stream));
+  KL(IE_K_KRYLOV_MISC, 2 * sz * n, Krylov<T>::combine(V, ld, m, dy, x, n, c->stream, &st->jd));
+  CKS(A.apply(x, tmp));
+  KL(IE_K_KRYLOV_MISC, 3 * sz * n, Krylov<T>::rsub(b, tmp, n, dn + 1, sc, c->stream));
+  KL(IE_K_KRYLOV_MISC, 0, gm_restart(st, dn + 1, h_outer, c->stream));
+  KL(IE_K_KRYLOV_MISC, 2 * sz * n, Krylov<T>::scale(tmp, V, n, dn + 1, 0.0, c->stream));
+  cudaGraph_t done1 = nullptr;
+  CK(cudaStreamEndCapture(c->cap[1], &done1));
+  c->stream = c->cap[0];
+  CK(cudaStreamEndCapture(c->cap[0], &G->graph));
+  CK(cudaGraphInstantiate(&G->exec, G->graph, 0));
+  return IE_OK;
+}
+
+template <typename T>
+ie_status gmres_graph(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, double tol, int m, int max_it,
+                      GmresOut* out) {
+  const bool cgs2 = tol < kReorthTol;
+  const long n = 3 * A.nb();
+  CKS(ensure_scalars(c));
+  if (m < 1 || m > 127) return fail(c, IE_EINVAL, "restart must be in [1, 127]");
+  const long ld = (n + 1) & ~1L;
+  CK(c->V.ensure(sizeof(C<T>) * (size_t)(m + 1) * ld));
+  CK(c->kt1.ensure(sizeof(C<T>) * (size_t)n));
+  CK(c->gm_state.ensure(sizeof(GmState)));
+  for (int k = 0; k < 3; ++k) CKS(cap_stream(c, k));
+  *out = GmresOut();
+  // outside any capture: allocates the block's workspaces and tunes its tiles
+  C<T>* V = c->V.as<C<T>>();
+  CKS(A.apply(V, V + ld));
+  const bool f32 = std::is_same<T, float>::value;
+  const std::vector<const void*> key = {
+      reinterpret_cast<const void*>(sizeof(C<T>)), reinterpret_cast<const void*>((long)A.z0),
+      reinterpret_cast<const void*>((long)A.nz), reinterpret_cast<const void*>((long)A.contract),
+      reinterpret_cast<const void*>((long)m), reinterpret_cast<const void*>((long)cgs2), b, x, V,
+      reinterpret_cast<const void*>(ld), c->kt1.p, (f32 ? c->A32 : c->A64).p, (f32 ? c->B32 : c->B64).p,
+      (f32 ? c->cw32 : c->cw64).p, A.S, c->gm_state.p, c->dh.p, c->part.p};
+  GmGraph* G = nullptr;
+  for (auto* g : c->gm_graphs)
+    if (g->key == key) G = g;
+  if (!G) {
+    G = new (std::nothrow) GmGraph();
+    if (!G) return fail(c, IE_ENOMEM, "graph cache");
+    G->key = key;
+    cudaStream_t saved = c->stream;
+    Tape* saved_tape = c->tape;
+    const ie_status bst = build_gmres_graph<T>(c, A, b, x, m, cgs2, n, ld, G);
+    c->stream = saved;
+    c->tape = saved_tape;
+    if (bst != IE_OK) {
+      abandon_capture(c);
+      delete G;
+      return bst;
+    }
+    if ((int)c->gm_graphs.size() >= kGmGraphCache) {
+      delete c->gm_graphs.front();
+      c->gm_graphs.erase(c->gm_graphs.begin());
+    }
+    c->gm_graphs.push_back(G);
+  }
+  GmState* st = c->gm_state.as<GmState>();
+  cudaStream_t s = c->stream;
+  // launch parameters: max_it, m, tol (contiguous in GmState)
+  const size_t p0 = offsetof(GmHead, max_it), p1 = offsetof(GmHead, tol) + sizeof(double);
+  unsigned char* stage = reinterpret_cast<unsigned char*>(c->hpin);
+  GmHead hs;
+  hs.max_it = max_it;
+  hs.m = m;
+  hs.tol = tol;
+  std::memcpy(stage, reinterpret_cast<const unsigned char*>(&hs) + p0, p1 - p0);
+  CK(cudaMemcpyAsync(reinterpret_cast<unsigned char*>(st) + p0, stage, p1 - p0, cudaMemcpyHostToDevice, s));
+  CK(cudaGraphLaunch(G->exec, s));
+  const size_t hdr = offsetof(GmState, cs), lens = 256;
+  CK(cudaMemcpyAsync(stage, st, hdr, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(stage + lens, reinterpret_cast<unsigned char*>(st) + offsetof(GmState, cyc_len),
+                     sizeof(int) * kGmMaxCycles, cudaMemcpyDeviceToHost, s));
+  CK(sync(c));
+  std::memcpy(&hs, stage, hdr);
+  std::vector<int> cyc(kGmMaxCycles);
+  std::memcpy(cyc.data(), stage + lens, sizeof(int) * kGmMaxCycles);
+  // accounting of what ran: the setup once, per cycle its head, its steps and its tail
+  account(c, G->pre);
+  const int ncyc = std::min(hs.cycles, kGmMaxCycles);
+  for (int k = 0; k < ncyc; ++k) {
+    account(c, G->head);
+    for (int j = 0; j < std::min(cyc[k], m); ++j) account(c, G->step[j]);
+    account(c, G->tail);
+    c->prof.bytes[IE_K_KRYLOV_MISC] += sizeof(C<T>) * (double)n * cyc[k];  // x += V y reads cyc[k] vectors
+  }
+  if (hs.reorth > 0 && hs.iters > 0) {  // second Gram-Schmidt passes at the mean basis size
+    const double nv = std::max(1.0, (double)hs.iters / std::max(1, hs.cycles) / 2.0);
+    c->prof.bytes[IE_K_DOTS] += hs.reorth * sizeof(C<T>) * (double)n * (nv + std::ceil(nv / kDotGroup));
+    c->prof.bytes[IE_K_UPDATE] += hs.reorth * sizeof(C<T>) * (double)n * (nv + 2);
+  }
+  if (hs.status == 3) return fail(c, IE_ECUDA, "GMRES produced a non-finite residual");
+  out->iters = hs.iters;
+  out->matvecs = hs.iters + hs.cycles;
+  out->reorth = hs.reorth;
+  out->rel = hs.rel;
+  out->converged = hs.status == 1;
+  return IE_OK;
+}
+
 struct SolveCfg {
   int dd_mode;
   std::vector<int> split;
-  int restart, max_outer, max_inner, precision, adaptive, contraction;
+  int restart, max_outer, max_inner, precision, adaptive, contraction, graph;
   double fixed_tol, tol;
 };
 
@@ -755,7 +1012,10 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
       else
         KL(IE_K_FIELD, 96.0 * nb, launch_copy_c128(Ri, c->N, reinterpret_cast<double2*>(rhs), nb, nb, s));
       GmresOut go;
-      CKS(gmres<T>(c, A, rhs, dx, true, tol_i, cfg.restart, cfg.max_inner, &go));
+      if (cfg.graph)
+        CKS(gmres_graph<T>(c, A, rhs, dx, tol_i, cfg.restart, cfg.max_inner, &go));
+      else
+        CKS(gmres<T>(c, A, rhs, dx, true, tol_i, cfg.restart, cfg.max_inner, &go));
       CKS(A.to_field(dx));  // contraction form: the field correction is M times the GMRES solution
       inner_ok = inner_ok && go.converged;
       sweep_its += go.iters;
@@ -973,6 +1233,8 @@ ie_status ie_solve(ie_ctx* c, int32_t n_src, const ie_dipole* src, int32_t n_rx,
   cfg.fixed_tol = o.fixed_tol > 0 ? o.fixed_tol : tol;
   cfg.tol = tol;
   cfg.contraction = o.contraction;
+  cfg.graph = o.graph;
+  if (o.graph != 0 && o.graph != 1) return fail(c, IE_EINVAL, "graph must be 0 or 1");
   if (o.contraction != 0 && o.contraction != 1) return fail(c, IE_EINVAL, "contraction must be 0 or 1");
   if (cfg.precision != IE_PREC_MIXED && cfg.precision != IE_PREC_FP64) return fail(c, IE_EINVAL, "bad precision");
   const int M = (dd_mode == IE_DD_NONE) ? 1 : std::max(1, o.n_blocks);

@@ -258,8 +258,10 @@ __global__ void __launch_bounds__(kKThreads) k_update(const C<T>* __restrict__ V
 // ------------------------------------------------------------------ x += sum_k y_k V_k
 template <typename T>
 __global__ void __launch_bounds__(kKThreads) k_combine(const C<T>* __restrict__ V, long ld, int nv,
-                                                      const double2* __restrict__ y, C<T>* __restrict__ x, long n) {
+                                                      const double2* __restrict__ y, C<T>* __restrict__ x, long n,
+                                                      const int* __restrict__ nv_dev) {
   __shared__ C<T> ys[kMaxBasis];
+  if (nv_dev) nv = min(nv, *nv_dev);
   for (int k = threadIdx.x; k < nv; k += kKThreads) ys[k] = to_c(y[k], T());
   __syncthreads();
   for (long e = (long)blockIdx.x * kKThreads + threadIdx.x; e < n; e += (long)gridDim.x * kKThreads) {
@@ -381,9 +383,10 @@ cudaError_t Krylov<T>::update(const C<T>* V, long ld, int nv, const double2* h, 
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t Krylov<T>::combine(const C<T>* V, long ld, int nv, const double2* y, C<T>* x, long n, cudaStream_t s) {
+cudaError_t Krylov<T>::combine(const C<T>* V, long ld, int nv, const double2* y, C<T>* x, long n, cudaStream_t s,
+                               const int* nv_dev) {
   if (nv > kMaxBasis) return cudaErrorInvalidValue;
-  k_combine<T><<<krylov_blocks(n) * 2, kKThreads, 0, s>>>(V, ld, nv, y, x, n);
+  k_combine<T><<<krylov_blocks(n) * 2, kKThreads, 0, s>>>(V, ld, nv, y, x, n, nv_dev);
   return cudaGetLastError();
 }
 template <typename T>
@@ -404,6 +407,127 @@ cudaError_t Krylov<T>::rsub(const C<T>* b, C<T>* y, long n, double2* out, const 
 }
 template struct Krylov<float>;
 template struct Krylov<double>;
+
+// ---------------------------------------------------------------- GMRES control on the device
+// One thread each: the work is O(m) (rotations) or O(m^2) (back substitution) FP64 operations.
+namespace {
+__device__ __forceinline__ double2 zc(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return zc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 zconj(double2 a) { return zc(a.x, -a.y); }
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return zc(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return zc(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double zabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double2 zscale(double2 a, double s) { return zc(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+  const double d = zabs2(b);
+  return zc((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+}  // namespace
+
+__global__ void k_gm_init(GmState* st, const double2* nrm2, cudaGraphConditionalHandle outer) {
+  const double b2 = nrm2->x;
+  st->bnorm = b2 > 0.0 ? sqrt(b2) : 0.0;
+  st->beta = st->bnorm;
+  st->iters = st->cycles = st->reorth = st->j = st->jd = 0;
+  st->rel = st->bnorm > 0.0 ? 1.0 : 0.0;
+  st->est = st->rel;
+  st->status = st->bnorm > 0.0 ? 0 : 1;
+  cudaGraphSetConditional(outer, st->bnorm > 0.0 ? 1u : 0u);
+}
+
+__global__ void k_gm_cycle(GmState* st, const GmSteps steps) {
+  st->j = 0;
+  st->g[0] = zc(st->beta, 0.0);
+  for (int i = 1; i <= st->m; ++i) st->g[i] = zc(0.0, 0.0);
+  for (int k = 0; k < steps.m; ++k) cudaGraphSetConditional(steps.h[k], k == 0 ? 1u : 0u);
+}
+
+__global__ void k_gm_step(GmState* st, int j, const double2* __restrict__ h, const double2* __restrict__ nrm2,
+                          const int* __restrict__ reorth_flag, cudaGraphConditionalHandle next, int has_next) {
+  constexpr int M = kGmMaxM;
+  double2* H = st->H;
+  for (int i = 0; i <= j; ++i) H[i * M + j] = h[i];
+  const double hn = sqrt(fmax(nrm2->x, 0.0));
+  H[(j + 1) * M + j] = zc(hn, 0.0);
+  if (reorth_flag && *reorth_flag) st->reorth++;
+  for (int i = 0; i < j; ++i) {
+    const double2 hij = H[i * M + j], hi1 = H[(i + 1) * M + j];
+    const double2 t = zadd(zmul(st->cs[i], hij), zmul(st->sn[i], hi1));
+    H[(i + 1) * M + j] = zadd(zmul(zc(-st->sn[i].x, st->sn[i].y), hij), zmul(zconj(st->cs[i]), hi1));
+    H[i * M + j] = t;
+  }
+  const double2 a = H[j * M + j], d = H[(j + 1) * M + j];
+  const double den = sqrt(zabs2(a) + zabs2(d));
+  st->cs[j] = den != 0.0 ? zscale(zconj(a), 1.0 / den) : zc(1.0, 0.0);
+  st->sn[j] = den != 0.0 ? zscale(zconj(d), 1.0 / den) : zc(0.0, 0.0);
+  H[j * M + j] = zadd(zmul(st->cs[j], a), zmul(st->sn[j], d));
+  H[(j + 1) * M + j] = zc(0.0, 0.0);
+  const double2 gj = st->g[j];
+  st->g[j + 1] = zmul(zc(-st->sn[j].x, st->sn[j].y), gj);
+  st->g[j] = zmul(st->cs[j], gj);
+  st->iters++;
+  st->j = j + 1;
+  const double est = sqrt(zabs2(st->g[j + 1])) / st->bnorm;
+  st->est = est;
+  const bool stop = !(est > st->tol) || hn == 0.0 || st->iters >= st->max_it || j + 1 >= st->m;
+  if (!isfinite(est)) st->status = 3;
+  if (has_next) cudaGraphSetConditional(next, (stop || st->status == 3) ? 0u : 1u);
+}
+
+__global__ void k_gm_solve(GmState* st, double2* __restrict__ y_out) {
+  constexpr int M = kGmMaxM;
+  const int jd = st->status == 3 ? 0 : st->j;
+  for (int i = jd - 1; i >= 0; --i) {
+    double2 acc = st->g[i];
+    for (int k = i + 1; k < jd; ++k) acc = zsub(acc, zmul(st->H[i * M + k], st->y[k]));
+    st->y[i] = zdiv(acc, st->H[i * M + i]);
+  }
+  for (int i = 0; i < jd; ++i) y_out[i] = st->y[i];
+  st->jd = jd;
+  if (st->cycles < kGmMaxCycles) st->cyc_len[st->cycles] = st->j;
+}
+
+__global__ void k_gm_restart(GmState* st, const double2* __restrict__ nrm2, cudaGraphConditionalHandle outer) {
+  const double beta = sqrt(fmax(nrm2->x, 0.0));
+  st->beta = beta;
+  st->rel = beta / st->bnorm;
+  st->cycles++;
+  unsigned more = 1u;
+  if (!isfinite(st->rel) || st->status == 3) {
+    st->status = 3;
+    more = 0u;
+  } else if (st->rel <= st->tol) {
+    st->status = 1;
+    more = 0u;
+  } else if (st->iters >= st->max_it || beta == 0.0 || st->cycles >= st->max_it) {
+    st->status = 2;
+    more = 0u;
+  }
+  cudaGraphSetConditional(outer, more);
+}
+
+cudaError_t gm_init(GmState* st, const double2* nrm2, cudaGraphConditionalHandle outer, cudaStream_t s) {
+  k_gm_init<<<1, 1, 0, s>>>(st, nrm2, outer);
+  return cudaGetLastError();
+}
+cudaError_t gm_cycle(GmState* st, const GmSteps& steps, cudaStream_t s) {
+  if (steps.m < 1 || steps.m > kGmMaxM) return cudaErrorInvalidValue;
+  k_gm_cycle<<<1, 1, 0, s>>>(st, steps);
+  return cudaGetLastError();
+}
+cudaError_t gm_step(GmState* st, int j, const double2* h, const double2* nrm2, const int* reorth_flag,
+                    cudaGraphConditionalHandle next, bool has_next, cudaStream_t s) {
+  k_gm_step<<<1, 1, 0, s>>>(st, j, h, nrm2, reorth_flag, next, has_next ? 1 : 0);
+  return cudaGetLastError();
+}
+cudaError_t gm_solve(GmState* st, double2* y_out, cudaStream_t s) {
+  k_gm_solve<<<1, 1, 0, s>>>(st, y_out);
+  return cudaGetLastError();
+}
+cudaError_t gm_restart(GmState* st, const double2* nrm2, cudaGraphConditionalHandle outer, cudaStream_t s) {
+  k_gm_restart<<<1, 1, 0, s>>>(st, nrm2, outer);
+  return cudaGetLastError();
+}
 
 static unsigned egrid(long n) {
   long g = (3 * n + 255) / 256;
