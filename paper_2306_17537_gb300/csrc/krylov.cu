@@ -15,8 +15,10 @@ namespace ie {
 constexpr int kKThreads = 256;
 constexpr int kMaxBasis = 128;
 
+// Blocks for an n-element Krylov kernel: at least 4 packets per thread before the grid reaches
+// kRedBlocks, so small sub-domains do not pay for hundreds of partial sums.
 int krylov_blocks(long n) {
-  long g = (n / 2 + kKThreads - 1) / kKThreads;
+  long g = (n / 2 + 4L * kKThreads - 1) / (4L * kKThreads);
   if (g > kRedBlocks) g = kRedBlocks;
   if (g < 1) g = 1;
   return (int)g;
@@ -117,6 +119,12 @@ __device__ __forceinline__ double2 sum_partials(const double2* part, int nblk, d
   for (int b = threadIdx.x; b < nblk; b += kKThreads) s = s + __ldcg(part + b);
   return block_sum(s, red);
 }
+// Fixed-order sum of the partials of one slot by one warp; result in lane 0.
+__device__ __forceinline__ double2 warp_sum_partials(const double2* part, int nblk) {
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = threadIdx.x & 31; b < nblk; b += 32) s = s + __ldcg(part + b);
+  return warp_sum(s);
+}
 
 // ------------------------------------------------------------------ inner products V^H w (+ |w|^2)
 template <typename T>
@@ -183,11 +191,12 @@ __global__ void __launch_bounds__(kKThreads) k_dots(const C<T>* __restrict__ V, 
     if (threadIdx.x == 0) part[(long)nv * kRedBlocks + blockIdx.x] = s;
   }
   if (!arrive_last(counters + g, gridDim.x)) return;
-  for (int q = 0; q <= nk; ++q) {
+  // the group's slots (and the norm) in parallel, one warp per slot
+  const int nslots = nk + (dn ? 1 : 0);
+  for (int q = threadIdx.x >> 5; q < nslots; q += kKThreads / 32) {
     const int slot = (q < nk) ? k0 + q : nv;
-    if (q == nk && !dn) break;
-    const double2 s = sum_partials(part + (long)slot * kRedBlocks, gridDim.x, red);
-    if (threadIdx.x == 0) {
+    const double2 s = warp_sum_partials(part + (long)slot * kRedBlocks, gridDim.x);
+    if ((threadIdx.x & 31) == 0) {
       out[slot] = s;
       if (acc && slot < nv) acc[slot] = acc[slot] + s;
     }
