@@ -3,8 +3,10 @@
 
 Workload (the paper's logging window 1 shape, Section 3.3): 128 x 128 x 256 cells of 0.25 m split
 into two 128^3 sub-domains along z, block Gauss-Seidel with the adaptive sub-domain tolerance e/10
-(Algorithm 1), complex64 FFT convolution and Krylov vectors with FP64 whole-grid residual and
-refinement, target e <= 1e-6 (eq. 9) verified in FP64; five dipping TI layers (anisotropy ratio
+(Algorithm 1), each block solved by GMRES on the contraction form of the IE operator (the default;
+``--operator conventional`` runs the paper's conventional form, which the line also reports as a
+variant), complex64 FFT convolution and Krylov vectors with FP64 whole-grid residual and
+refinement, target e <= 1e-6 (eq. 9, the conventional residual) verified in FP64; five dipping TI layers (anisotropy ratio
 1-10, Appendix C rotation) plus two isotropic ellipsoids, seeded; coaxial z magnetic dipole with
 receivers at 0.5/1/2 m; f = 400 kHz, sigma0 = 0.1 S/m. Synthetic data: the paper's formations
 exist only in figures.
@@ -35,10 +37,11 @@ if ROOT not in sys.path:
 METRIC = "IE forward solves/sec at 1e-6 rel. residual; matvec HBM GB/s vs peak"
 UNIT = "solves/s"
 WORKLOAD = "DD 128x128x256 @0.25 m, 2 sub-domains block Gauss-Seidel adaptive (GS-A), 5 dipping TI layers + 2 ellipsoids, 1 coaxial tool position, 400 kHz, tol 1e-6"
-# Operator applications of one oracle-sized solve, used only to scale the CPU oracle sample of the
-# reference arm to solves/s (the GB300 arm counts them live, "CPU baseline").
-REF_BLOCK_APPLICATIONS_PER_SOLVE = 2000
-REF_FULL_APPLICATIONS_PER_SOLVE = 20
+# Sub-domain operator applications of one solve of this workload per operator form (GMRES steps,
+# restart residuals and the 10 interaction updates of the GS-A solve, as the GB300 arm counts them) and
+# whole-grid applications (one FP64 residual per sweep plus the initial one), used only to scale the
+# CPU oracle sample of the reference arm, which runs without the GB300 arm, to solves/s.
+REF_APPLICATIONS_PER_SOLVE = {"contraction": (260, 11), "conventional": (650, 11)}
 
 
 def parse():
@@ -51,6 +54,8 @@ def parse():
     ap.add_argument("--scale", type=int, default=1, help="divide the grid by this factor (testing only)")
     ap.add_argument("--restart", type=int, default=None, help="GMRES restart length (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--operator", default="contraction", choices=["contraction", "conventional"],
+                    help="operator form GMRES iterates on inside the sub-domain solves")
     return ap.parse_args()
 
 
@@ -161,15 +166,19 @@ def traffic_record(kernel_class: str):
 
 
 # ------------------------------------------------------------------------------------ CPU oracle
-def oracle_block_sample(wl, z0, nz, n_apply=1):
-    """Time the CPU oracle's operator of one sub-domain: spectra setup + n_apply applications."""
+def oracle_block_sample(wl, z0, nz, n_apply=1, contraction=True):
+    """Time the CPU oracle's operator of one sub-domain (the contraction or the conventional form):
+    spectra setup + n_apply applications."""
     import numpy as np
 
+    from oracle import contraction as oc
     from oracle import operator as oop
 
     t0 = time.perf_counter()
-    dsig = oop.contrast(wl.sigma6[z0:z0 + nz], wl.sigma0)
-    op = oop.FFTOperator(dsig, wl.grid.h, wl.freq, wl.sigma0)
+    if contraction:
+        op = oc.ContractionOperator(wl.sigma6[z0:z0 + nz], wl.grid.h, wl.freq, wl.sigma0)
+    else:
+        op = oop.FFTOperator(oop.contrast(wl.sigma6[z0:z0 + nz], wl.sigma0), wl.grid.h, wl.freq, wl.sigma0)
     t1 = time.perf_counter()
     x = np.ones((3, nz, wl.grid.ny, wl.grid.nx), dtype=np.complex128)
     for _ in range(n_apply):
@@ -206,8 +215,9 @@ def run_gb300(args):
     s6_dev = torch.from_numpy(np.ascontiguousarray(wl.sigma6)).to(dev)
     if args.restart:
         wl.restart = args.restart
+    contraction = args.operator == "contraction"
     opts = ie.make_opts(z_split=wl.z_split, restart=wl.restart, precision=ie.IE_PREC_MIXED, max_inner=4000,
-                        max_outer=60)
+                        max_outer=60, contraction=contraction)
     src, rx = wl.sources, wl.receivers
 
     def step_dev():
@@ -256,6 +266,29 @@ def run_gb300(args):
     e2e_value = job_throughput(e2e_steps, world, max_over_ranks(e0.elapsed_time(e1), dev))
     h2d = s6_host.nbytes + rx.nbytes + 48 * len(src)
     d2h = H2.nbytes
+    # ----------------------------------------------------------------- the other operator form
+    other = "conventional" if contraction else "contraction"
+    vopts = ie.make_opts(z_split=wl.z_split, restart=wl.restart, precision=ie.IE_PREC_MIXED, max_inner=4000,
+                         max_outer=60, contraction=not contraction)
+    ctx.set_contrast_dev(s6_dev)
+    ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, vopts)
+    v_steps = max(1, min(args.steps, 2))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    v0.record(stream)
+    for _ in range(v_steps):
+        ctx.set_contrast_dev(s6_dev)
+        Hv, vinfo, vst = ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, vopts)
+    v1.record(stream)
+    torch.cuda.synchronize(dev)
+    v_ms = max_over_ranks(v0.elapsed_time(v1), dev)
+    variant = {"operator": other, "value": round(job_throughput(v_steps, world, v_ms), 4), "unit": UNIT,
+               "steps": v_steps, "ms_per_step": round(v_ms / v_steps, 2), "status": int(vst),
+               "outer_iters": vinfo.outer_iters, "gmres_iters": vinfo.gmres_iters_total,
+               "final_rel_residual": vinfo.final_rel_residual,
+               "max_rel_diff_H_vs_headline": float(np.max(np.abs(Hv - H)) / np.max(np.abs(H)))}
     # ----------------------------------------------------------------- block operator bandwidth
     nb = 3 * (g.nz // 2) * g.ny * g.nx
     x = torch.randn(nb, dtype=torch.complex64, device=dev)
@@ -296,7 +329,7 @@ def run_gb300(args):
     # ----------------------------------------------------------------- CPU oracle baseline
     cpu_baseline = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_setup, t_apply = oracle_block_sample(wl, 0, g.nz // 2, n_apply=1)
+        t_setup, t_apply = oracle_block_sample(wl, 0, g.nz // 2, n_apply=1, contraction=contraction)
         # whole-grid applications (FP64 residual) cost about twice a sub-domain one (twice the volume)
         applications = last.matvecs + 2 * (last.outer_iters + 1) + last.outer_iters
         est = 3 * t_setup + t_apply * applications
@@ -312,6 +345,7 @@ def run_gb300(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic (seeded generator)",
         "config": {"workload": WORKLOAD, "grid": [g.nx, g.ny, g.nz], "h_m": g.h, "sub_domains": wl.z_split,
                    "dd": "block Gauss-Seidel, adaptive tol e/10", "precision": "complex64 conv/Krylov + FP64 refinement",
+                   "operator": args.operator,
                    "restart": wl.restart, "tol": wl.tol, "freq_hz": wl.freq, "sigma0": wl.sigma0, "seed": args.seed,
                    "setup_s_excluded": round(setup_s, 3), "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"{world} independent tool positions (one per GPU)"},
@@ -326,6 +360,7 @@ def run_gb300(args):
                   "final_rel_residual": last.final_rel_residual,
                   "residual_history": [float(v) for v in last.history()],
                   "H_rx_z": [[float(H[0, r, 2].real), float(H[0, r, 2].imag)] for r in range(H.shape[1])]},
+        "variants": {other: variant},
         "kernels": breakdown,
         "tuned_tiles": ie.tuned_tiles().strip().splitlines(),
         "gpu_launches": gpu_launches,
@@ -342,7 +377,8 @@ def run_gb300(args):
 # ------------------------------------------------------------------------------------ reference arm
 def run_reference(args):
     """The CPU FP64 oracle as the reference: each step times one bounded sample (one application of
-    the 128^3 sub-domain operator) and converts it to solves/s with a fixed operator-application count."""
+    the 128^3 sub-domain operator in the selected form) and converts it to solves/s with a fixed
+    operator-application count."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -350,14 +386,18 @@ def run_reference(args):
 
     import numpy as np
 
+    from oracle import contraction as oc
     from oracle import operator as oop
 
     wl = inputs.config2(args.seed, scale=args.scale)
+    nzb = wl.grid.nz // 2
     t0 = time.perf_counter()
-    dsig = oop.contrast(wl.sigma6[: wl.grid.nz // 2], wl.sigma0)
-    op = oop.FFTOperator(dsig, wl.grid.h, wl.freq, wl.sigma0)
+    if args.operator == "contraction":
+        op = oc.ContractionOperator(wl.sigma6[:nzb], wl.grid.h, wl.freq, wl.sigma0)
+    else:
+        op = oop.FFTOperator(oop.contrast(wl.sigma6[:nzb], wl.sigma0), wl.grid.h, wl.freq, wl.sigma0)
     t_setup = time.perf_counter() - t0
-    x = np.ones((3, wl.grid.nz // 2, wl.grid.ny, wl.grid.nx), dtype=np.complex128)
+    x = np.ones((3, nzb, wl.grid.ny, wl.grid.nx), dtype=np.complex128)
     for _ in range(min(args.warmup, 1)):
         op(x)
     times = []
@@ -366,7 +406,8 @@ def run_reference(args):
         op(x)
         times.append(time.perf_counter() - t0)
     t_apply = sum(times) / len(times)
-    applications = REF_BLOCK_APPLICATIONS_PER_SOLVE + 2 * REF_FULL_APPLICATIONS_PER_SOLVE
+    n_block, n_full = REF_APPLICATIONS_PER_SOLVE[args.operator]
+    applications = n_block + 2 * n_full
     est = 3 * t_setup + t_apply * applications
     value = 1.0 / est
     sample = (f"one application of the CPU FP64 oracle's 128^3 sub-domain operator per step (mean {t_apply:.2f} s) "
@@ -374,7 +415,7 @@ def run_reference(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(1e3 * t_apply, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded generator)",
-           "config": {"workload": WORKLOAD, "seed": args.seed}, "impl": "reference",
+           "config": {"workload": WORKLOAD, "seed": args.seed, "operator": args.operator}, "impl": "reference",
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
