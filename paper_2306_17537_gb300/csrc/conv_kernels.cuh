@@ -12,6 +12,7 @@
 #pragma once
 #include "conv.cuh"
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace ie {
 
@@ -156,27 +157,81 @@ template <typename T, int L, int WDIV = 1> struct P3Cfg {
   static constexpr int TT = Plan<T, L>::TT;
   static constexpr int W0 = 128 / TT / WDIV;
   static constexpr int W = W0 < 1 ? 1 : (W0 > 32 ? 32 : W0);
+  // TMA staging of the input pencils needs box rows of a multiple of 16 bytes (W lanes per row)
+  static constexpr bool kTmaOk = (W * (int)sizeof(C<T>)) % 16 == 0;
+  static constexpr int BZ = L < 256 ? L : 256;  // rows per TMA box (the box limit is 256)
+  // spectra + 3 mbarriers + room to align the TMA destinations to 128 bytes
+  static constexpr size_t kTmaSmem = 3 * (size_t)L * W * sizeof(C<T>) + 64 + 128;
 };
 
-template <typename T, int L, int WDIV>
+// TMA: all three components' input pencils (W lanes x L positions, the zero padding and positions
+// outside the source slab filled by the copy engine) are staged into the spectrum buffers by
+// asynchronous tensor copies issued at kernel start, so the loads of components 1 and 2 overlap the FFT
+// of component 0. Otherwise each component is loaded into registers just before its FFT. A staging
+// wait that exceeds its spin limit sets *err, waits (bounded) for the other copies and ends the block.
+template <typename T, int L, int WDIV, bool TMA>
 __global__ void __launch_bounds__(128, 4) k_p3_spectral(
     const C<T>* __restrict__ Bin, long in_cs, int nzs, int os, C<T>* __restrict__ Bout, long out_cs,
-    int nzt, int ot, const C<T>* __restrict__ G, int Lx, int Ly, const C<T>* __restrict__ tw) {
-  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = P3Cfg<T, L, WDIV>::W;
-  __shared__ C<T> spec[3][L * W];
+    int nzt, int ot, const C<T>* __restrict__ G, int Lx, int Ly, const C<T>* __restrict__ tw,
+    const __grid_constant__ CUtensorMap tmap, int* __restrict__ err) {
+  using Cfg = P3Cfg<T, L, WDIV>;
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = Cfg::W;
+  constexpr bool kTma = TMA && Cfg::kTmaOk;
+  C<T>* spec_base;
+  uint64_t* bar = nullptr;
+  if constexpr (kTma) {
+    extern __shared__ __align__(128) unsigned char p3_dyn[];
+    unsigned char* base = p3_dyn + ((128u - (smem_addr(p3_dyn) & 127u)) & 127u);
+    spec_base = reinterpret_cast<C<T>*>(base);
+    bar = reinterpret_cast<uint64_t*>(base + 3 * (size_t)L * W * sizeof(C<T>));
+  } else {
+    __shared__ C<T> p3_static[3 * L * W];
+    spec_base = p3_static;
+  }
+  auto spec = [spec_base](int c) { return spec_base + c * (L * W); };
   const int w = threadIdx.x, t = threadIdx.y;
   const int kx = blockIdx.x * W + w, ky = blockIdx.y;
   const bool act = kx < Lx;
   const long plane = (long)Ly * Lx, off = (long)ky * Lx + kx;
   C<T> v[E];
+  if constexpr (kTma) {
+    const int tid = t * W + w;
+    if (tid == 0) {
+      for (int c = 0; c < 3; ++c) mbar_init(bar + c, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      constexpr int R = (int)sizeof(C<T>) / 8;  // 8-byte tensor elements per complex value
+      for (int c = 0; c < 3; ++c) {
+        mbar_expect_tx(bar + c, (unsigned)(L * W * sizeof(C<T>)));
+        for (int k = 0; k < L / Cfg::BZ; ++k)
+          tma_load_4d(spec(c) + (size_t)k * Cfg::BZ * W, &tmap, (int)blockIdx.x * W * R, ky, k * Cfg::BZ - os, c,
+                      bar + c);
+      }
+    }
+  }
   // forward z-FFT of each component; spectrum left in spec[c] at the thread's own positions
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
-    LaneSM<T, W> sm{spec[c] + w};
+    LaneSM<T, W> sm{spec(c) + w};
+    if constexpr (kTma) {
+      if (!__syncthreads_and(mbar_wait(bar + c, 0))) {
+        if (t == 0 && w == 0) {
+          atomicExch(err, 1);
+          for (int c2 = c + 1; c2 < 3; ++c2) mbar_wait(bar + c2, 0);
+        }
+        return;
+      }
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int z = t + TT * m - os;
-      v[m] = (act && z >= 0 && z < nzs) ? Bin[c * in_cs + z * plane + off] : czero<C<T>>();
+      for (int m = 0; m < E; ++m) v[m] = spec(c)[(t + TT * m) * W + w];  // staged rows are dense
+      __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]
+    } else {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int z = t + TT * m - os;
+        v[m] = (act && z >= 0 && z < nzs) ? Bin[c * in_cs + z * plane + off] : czero<C<T>>();
+      }
     }
     pencil_fft<T, L, -1>(v, t, sm, tw);
 #pragma unroll
@@ -194,7 +249,7 @@ __global__ void __launch_bounds__(128, 4) k_p3_spectral(
     const bool xlo = kx <= Lx / 2, ylo = ky <= Ly / 2;
     const int ix = xlo ? kx : Lx - kx, iy = ylo ? ky : Ly - ky;
     const C<T>* gb = G + (long)iy * ox + ix;
-    LaneSM<T, W> s0{spec[0] + w}, s1{spec[1] + w}, s2{spec[2] + w};
+    LaneSM<T, W> s0{spec(0) + w}, s1{spec(1) + w}, s2{spec(2) + w};
     if (act) {
 #pragma unroll
       for (int m = 0; m < E; ++m) {
@@ -223,7 +278,7 @@ __global__ void __launch_bounds__(128, 4) k_p3_spectral(
   // inverse z-FFT of each component and crop
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
-    LaneSM<T, W> sm{spec[c] + w};
+    LaneSM<T, W> sm{spec(c) + w};
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = sm.ld(t + TT * m);
     __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]

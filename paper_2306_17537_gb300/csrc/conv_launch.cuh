@@ -5,6 +5,10 @@
 #include "conv.cuh"
 #include "conv_kernels.cuh"
 
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
 #include <type_traits>
 
 namespace ie {
@@ -127,24 +131,74 @@ cudaError_t ConvLaunch<T>::lanes(int L, int sign, int variant, const C<T>* in, l
   }
 }
 
-template <typename T, int N, int WDIV>
+// cuTensorMapEncodeTiled from the driver, looked up once (null when the driver does not provide it).
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// TMA = true stages the input pencils with tensor copies when the tile allows it (P3Cfg::kTmaOk) and
+// the driver provides the tensor-map encoder; otherwise the same tile runs with register loads.
+template <typename T, int N, int WDIV, bool TMA>
 static cudaError_t p3_launch(const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt, int ot,
-                             const C<T>* G, int Lx, int Ly, const C<T>* tw, cudaStream_t s) {
-  constexpr int W = P3Cfg<T, N, WDIV>::W;
+                             const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err, cudaStream_t s) {
+  using Cfg = P3Cfg<T, N, WDIV>;
+  constexpr int W = Cfg::W;
   dim3 blk(W, Plan<T, N>::TT), grd((unsigned)((Lx + W - 1) / W), (unsigned)Ly);
-  k_p3_spectral<T, N, WDIV><<<grd, blk, 0, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw);
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  if constexpr (TMA && Cfg::kTmaOk) {
+    auto enc = tensor_map_encoder();
+    if (enc) {
+      // B viewed as 8-byte elements: (x = Lx * R, y = Ly, z = nzs source rows, component)
+      constexpr int R = (int)sizeof(C<T>) / 8;
+      const cuuint64_t dims[4] = {(cuuint64_t)Lx * R, (cuuint64_t)Ly, (cuuint64_t)nzs, 3};
+      const cuuint64_t strides[3] = {(cuuint64_t)Lx * R * 8, (cuuint64_t)Ly * Lx * R * 8, (cuuint64_t)in_cs * R * 8};
+      const cuuint32_t box[4] = {(cuuint32_t)(W * R), 1, (cuuint32_t)Cfg::BZ, 1};
+      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<C<T>*>(Bin), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+      static std::once_flag attr;
+      cudaError_t ae = cudaSuccess;
+      std::call_once(attr, [&] {
+        ae = cudaFuncSetAttribute(k_p3_spectral<T, N, WDIV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Cfg::kTmaSmem);
+      });
+      if (ae != cudaSuccess) return ae;
+      k_p3_spectral<T, N, WDIV, true><<<grd, blk, Cfg::kTmaSmem, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G,
+                                                                      Lx, Ly, tw, map, err);
+      return cudaGetLastError();
+    }
+  }
+  k_p3_spectral<T, N, WDIV, false><<<grd, blk, 0, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw,
+                                                       map, err);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t ConvLaunch<T>::p3(int L, int variant, const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout,
-                              long out_cs, int nzt, int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw,
+                              long out_cs, int nzt, int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err,
                               cudaStream_t s) {
   switch (L) {
-#define IE_CASE(N)                                                                                             \
-  case N:                                                                                                      \
-    return variant ? p3_launch<T, N, 2>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, s)          \
-                   : p3_launch<T, N, 1>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, s);
+#define IE_CASE(N)                                                                                                 \
+  case N:                                                                                                          \
+    switch (variant) {                                                                                             \
+      case 1: return p3_launch<T, N, 2, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
+      case 2: return p3_launch<T, N, 1, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
+      case 3: return p3_launch<T, N, 2, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
+      default: return p3_launch<T, N, 1, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
+    }
     IE_FOR_EACH_L(IE_CASE)
 #undef IE_CASE
     default:

@@ -123,6 +123,7 @@ struct ie_ctx {
   DevBuf V, kx, kb, kt1, kt2;
   DevBuf part, counters, dh, dh2, dnrm, dy, flag, rxdev, Hdev, rxpart;
   double2* hpin = nullptr;  // pinned host scratch for small reductions
+  int* kerr = nullptr;      // mapped pinned flag: a kernel's bounded wait gave up (checked at every sync)
 
   struct Prof {  // launch accounting (ie_profile_enable / ie_profile_read)
     bool on = false;
@@ -139,6 +140,7 @@ struct ie_ctx {
       if (st) cudaStreamDestroy(st);
     for (auto* s : specs) delete s;
     if (hpin) cudaFreeHost(hpin);
+    if (kerr) cudaFreeHost(kerr);
     for (auto e : prof.ev) cudaEventDestroy(e);
   }
 };
@@ -208,6 +210,10 @@ cudaError_t drain(ie_ctx* c) {
 }
 cudaError_t sync(ie_ctx* c) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && c->kerr && *reinterpret_cast<volatile int*>(c->kerr)) {
+    *c->kerr = 0;
+    return cudaErrorLaunchTimeout;  // a staging wait in a kernel reached its spin limit
+  }
   return e == cudaSuccess ? drain(c) : e;
 }
 
@@ -304,8 +310,9 @@ template <typename T> ie_status ensure_conv_ws(ie_ctx* c, int zcap) {
 }
 
 // ------------------------------------------------------------------ FFT tile autotuner
-// The strided passes (P2, P3, P4) have two tile shapes (kTileVariants): the default and one with half
-// the pencils per block. The first convolution of a new shape times every variant on the live buffers
+// The strided passes (P2, P3, P4) have two tile shapes: the default and one with half the pencils per
+// block; P3 has each also with TMA staging of its input pencils (four variants). The first convolution
+// of a new shape times every variant on the live buffers
 // (three timed launches each after a warm-up; the work is data independent) and keeps the fastest for
 // the rest of the process. Variants produce bit-identical results.
 struct TuneKey {
@@ -324,13 +331,13 @@ int tuned_variant(const TuneKey& k) {
 }
 
 // Time each variant of one launch (run(v) enqueues it on the context stream) and record the fastest.
-template <class F> cudaError_t tune(ie_ctx* c, const TuneKey& k, F&& run, int* best) {
+template <class F> cudaError_t tune(ie_ctx* c, const TuneKey& k, F&& run, int* best, int nvar = kTileVariants) {
   cudaEvent_t a, b;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   float best_ms = 1e30f;
   *best = 0;
-  for (int v = 0; v < kTileVariants && e == cudaSuccess; ++v) {
+  for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
     e = run(v);  // warm-up (module load, caches)
     if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
     for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = run(v);
@@ -396,7 +403,7 @@ ie_status conv(ie_ctx* c, const SpecSet* S, const FieldC<T>* x, long x_cs, int z
                                 c->Lx, c->Ly, c->Lx, nzs, 3, tw, s);
   };
   auto p3 = [&](int v) {
-    return ConvLaunch<T>::p3(S->Lz, v, B, B_cs, nzs, os, B, B_cs, nzt, ot, spec<T>(S), c->Lx, c->Ly, tw, s);
+    return ConvLaunch<T>::p3(S->Lz, v, B, B_cs, nzs, os, B, B_cs, nzt, ot, spec<T>(S), c->Lx, c->Ly, tw, c->kerr, s);
   };
   auto p4 = [&](int v) {
     return ConvLaunch<T>::lanes(c->Ly, +1, v, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx,
@@ -407,7 +414,7 @@ ie_status conv(ie_ctx* c, const SpecSet* S, const FieldC<T>* x, long x_cs, int z
   if (v2 < 0) CK(tune(c, k2, p2, &v2));
   KL(k0 + 1, 3 * sz * nzs * c->Lx * (double)(c->ny + c->Ly), p2(v2));
   if (v3 < 0) {  // P3 works in place: tune on the live B, then rebuild B from x before the real pass
-    CK(tune(c, k3, p3, &v3));
+    CK(tune(c, k3, p3, &v3, kP3TileVariants));
     CK(p1());
     CK(p2(v2));
   }
@@ -1140,6 +1147,12 @@ ie_status ie_create(const ie_grid* grid, double h, double sigma0, double freq, i
     delete c;
     return IE_EINVAL;
   }
+  if (cudaHostAlloc(reinterpret_cast<void**>(&c->kerr), sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+    c->kerr = nullptr;
+    delete c;
+    return IE_ENOMEM;
+  }
+  *c->kerr = 0;
   // twiddles exp(-2 pi i k / TWN) in FP64 (angles reduced to the first octant by symmetry)
   std::vector<double2> t64(TWN);
   std::vector<float2> t32(TWN);
@@ -1658,7 +1671,8 @@ extern "C" ie_status ie_matvec_dev_noalloc(ie_ctx* c, int32_t z0, int32_t nz, co
                            (long)nz * c->ny, tw, s));
   CK(ConvLaunch<float>::lanes(c->Ly, -1, 0, A, A_cs, (long)c->ny * c->Lx, c->Lx, c->ny, B, B_cs, (long)c->Ly * c->Lx,
                               c->Lx, c->Ly, c->Lx, nz, 3, tw, s));
-  CK(ConvLaunch<float>::p3(S->Lz, 0, B, B_cs, nz, 0, B, B_cs, nz, 0, S->G32.as<float2>(), c->Lx, c->Ly, tw, s));
+  CK(ConvLaunch<float>::p3(S->Lz, 0, B, B_cs, nz, 0, B, B_cs, nz, 0, S->G32.as<float2>(), c->Lx, c->Ly, tw, c->kerr,
+                           s));
   CK(ConvLaunch<float>::lanes(c->Ly, +1, 0, B, B_cs, (long)c->Ly * c->Lx, c->Lx, c->Ly, A, A_cs, (long)c->ny * c->Lx,
                               c->Lx, c->ny, c->Lx, nz, 3, tw, s));
   CK(ConvLaunch<float>::p5(c->Lx, EPI_APPLY, A, A_cs, c->nx, (long)nz * c->ny, x, nb, y, nb, nullptr, 0, nullptr, 0,
