@@ -110,6 +110,8 @@ cudaError_t gm_restart(GmState* st, const double2* nrm2, cudaGraphConditionalHan
 cudaError_t launch_c128_to_c64(const double2* src, long src_cs, float2* dst, long dst_cs, long n, cudaStream_t s);
 cudaError_t launch_add_c64_to_c128(const float2* src, long src_cs, double2* dst, long dst_cs, long n, cudaStream_t s);
 cudaError_t launch_add_c128(const double2* src, long src_cs, double2* dst, long dst_cs, long n, cudaStream_t s);
+// acc += a - b (contiguous complex64 vectors of n3 elements)
+cudaError_t launch_add_diff_c64(float2* acc, const float2* a, const float2* b, long n3, cudaStream_t s);
 cudaError_t launch_copy_c128(const double2* src, long src_cs, double2* dst, long dst_cs, long n, cudaStream_t s);
 // *out = |a + b|^2 over a 3-component strided field (b optional, complex64)
 cudaError_t launch_norm2_c128(const double2* a, long a_cs, const float2* b, long b_cs, long n, double2* out,

@@ -116,6 +116,7 @@ struct ie_ctx {
 
   DevBuf E, E0, R;  // c128 whole-grid fields
   DevBuf Ec64;      // complex64 copy of E for the early, complex64 residuals
+  DevBuf AEb;       // complex64 A_ii E_i of every block (block right-hand-side norms; see solve_one)
   bool has_field = false;
   DevBuf Einit;           // initial guess for the next solve (ie_set_initial_field_dev)
   bool has_init = false;
@@ -1003,6 +1004,25 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
   C<T>* rhs = c->kb.as<C<T>>();
   C<T>* dx = c->kx.as<C<T>>();
   C<T>* t2 = c->kt2.as<C<T>>();
+  // complex64 DD solves keep A_ii E_i of every block: formed once here, then advanced by A_ii delta =
+  // rhs - (final GMRES residual) after each block solve, so |b_i| = |R_i + A_ii E_i| costs a norm
+  // instead of an operator application per block and sweep
+  const bool keep_ae = std::is_same<T, float>::value && cfg.dd_mode != IE_DD_NONE;
+  std::vector<long> ae_off(M, 0);
+  if (keep_ae) {
+    long tot = 0;
+    for (int i = 0; i < M; ++i) {
+      ae_off[i] = tot;
+      tot += 3 * ops[i].nb();
+    }
+    CK(c->AEb.ensure(sizeof(float2) * tot));
+    for (int i = 0; i < M; ++i) {
+      const long nb = ops[i].nb(), off = (long)ops[i].z0 * nxy;
+      KL(IE_K_FIELD, 72.0 * nb,
+         launch_c128_to_c64(c->E.as<double2>() + off, c->N, reinterpret_cast<float2*>(dx), nb, nb, s));
+      CKS(ops[i].apply_conv(dx, reinterpret_cast<C<T>*>(c->AEb.as<float2>() + ae_off[i])));
+    }
+  }
   int sweeps = 0;
   bool inner_ok = true;
   while (e > cfg.tol && sweeps < cfg.max_outer) {
@@ -1020,7 +1040,9 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
       if (cfg.dd_mode == IE_DD_NONE) {
         CKS(norm_c128(c, c->E0.as<double2>(), c->N, nullptr, 0, c->N, &bnorm));
       } else {
-        if (std::is_same<T, float>::value) {
+        if (keep_ae) {
+          CKS(norm_c128(c, Ri, c->N, c->AEb.as<float2>() + ae_off[i], nb, nb, &bnorm));
+        } else if (std::is_same<T, float>::value) {
           KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(Ei, c->N, reinterpret_cast<float2*>(dx), nb, nb, s));
           CKS(A.apply_conv(dx, t2));
           CKS(norm_c128(c, Ri, c->N, reinterpret_cast<const float2*>(t2), nb, nb, &bnorm));
@@ -1044,6 +1066,10 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
         CKS(gmres_graph<T>(c, A, rhs, dx, tol_i, cfg.restart, cfg.max_inner, &go));
       else
         CKS(gmres<T>(c, A, rhs, dx, true, tol_i, cfg.restart, cfg.max_inner, &go));
+      if (keep_ae && go.iters > 0)  // A_ii delta = rhs - r with r = rhs - A x the final true residual (kt1)
+        KL(IE_K_FIELD, 96.0 * nb,
+           launch_add_diff_c64(c->AEb.as<float2>() + ae_off[i], reinterpret_cast<const float2*>(rhs),
+                               c->kt1.as<float2>(), 3 * nb, s));
       CKS(A.to_field(dx));  // contraction form: the field correction is M times the GMRES solution
       inner_ok = inner_ok && go.converged;
       sweep_its += go.iters;

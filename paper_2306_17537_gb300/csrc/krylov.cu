@@ -338,6 +338,12 @@ __global__ void k_add_c64_to_c128(const float2* __restrict__ src, long scs, doub
     dst[c * dcs + e] = dst[c * dcs + e] + to_c64(src[c * scs + e]);
   }
 }
+// acc += a - b on block-local complex64 vectors of 3n elements
+__global__ void k_add_diff_c64(float2* __restrict__ acc, const float2* __restrict__ a, const float2* __restrict__ b,
+                               long n3) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n3; i += (long)gridDim.x * blockDim.x)
+    acc[i] = acc[i] + (a[i] - b[i]);
+}
 __global__ void k_add_c128(const double2* __restrict__ src, long scs, double2* __restrict__ dst, long dcs, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 3 * n; i += (long)gridDim.x * blockDim.x) {
     const long c = i / n, e = i % n;
@@ -549,6 +555,10 @@ cudaError_t launch_c128_to_c64(const double2* src, long scs, float2* dst, long d
 }
 cudaError_t launch_add_c64_to_c128(const float2* src, long scs, double2* dst, long dcs, long n, cudaStream_t s) {
   k_add_c64_to_c128<<<egrid(n), 256, 0, s>>>(src, scs, dst, dcs, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_add_diff_c64(float2* acc, const float2* a, const float2* b, long n3, cudaStream_t s) {
+  k_add_diff_c64<<<egrid(n3 / 3 + 1), 256, 0, s>>>(acc, a, b, n3);
   return cudaGetLastError();
 }
 cudaError_t launch_add_c128(const double2* src, long scs, double2* dst, long dcs, long n, cudaStream_t s) {
