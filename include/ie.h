@@ -101,6 +101,9 @@ typedef struct {
   int32_t warm_start_used;   /* 1 if the guess of ie_set_initial_field_dev replaced E := E0 */
   double cold_rel_residual;  /* with a guess given: e (eq. 9) of E = E0 and of the guess; else 0 */
   double warm_rel_residual;
+  int32_t active_blocks;     /* sub-domains with contrast, summed over sources: only these are swept and
+                                e is measured over them (Section 3.1); the field of the others is
+                                E0 + G dsigma E from the final residual */
 } ie_info;
 
 typedef struct ie_ctx ie_ctx;

@@ -108,6 +108,19 @@ __global__ void k_set_contrast(const double* __restrict__ s6, long N, double sig
   }
 }
 
+// act[z] = 1 if any contrast component of plane z is non-zero (one block per plane).
+__global__ void k_plane_active(const double* __restrict__ d64, long N, long nxy, int* __restrict__ act) {
+  const long z = blockIdx.x;
+  int any = 0;
+  for (long i = threadIdx.x; i < nxy && !any; i += blockDim.x) {
+    const long o = z * nxy + i;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) any |= (d64[c * N + o] != 0.0);
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) act[z] = any;
+}
+
 // Contraction-form tensors from the contrast (both symmetric, [6][N], FP64 and FP32):
 //   M = 2 sigma0 (sigma + sigma0 I)^-1 = 2 sigma0 (dsigma + 2 sigma0 I)^-1,   K = dsigma M
 // (dsigma and M commute, so K is symmetric). The inverse is the adjugate over the determinant of the
@@ -292,6 +305,10 @@ cudaError_t launch_set_contrast(const double* s6, long N, double sigma0, double*
   return cudaGetLastError();
 }
 
+cudaError_t launch_plane_active(const double* d64, long N, long nxy, int nz, int* act, cudaStream_t s) {
+  k_plane_active<<<nz, 256, 0, s>>>(d64, N, nxy, act);
+  return cudaGetLastError();
+}
 cudaError_t launch_contract_tensors(const double* d64, long N, double sigma0, double* K64, double* M64, float* K32,
                                     float* M32, cudaStream_t s) {
   k_contract_tensors<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(d64, N, sigma0, K64, M64, K32, M32);

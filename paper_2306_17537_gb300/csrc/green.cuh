@@ -13,6 +13,8 @@ cudaError_t launch_green_tab(double2* out, int comp, int Lx, int Ly, int Lz, int
 // octant of the scaled spectrum in complex128, complex64 and double-float (odf: [n] x 16 bytes)
 cudaError_t launch_extract_octant(const double2* full, int Lx, int Ly, int Lz, double scale, double2* o64,
                                   float2* o32, void* odf, cudaStream_t s);
+// act[z] = 1 when plane z (nxy cells) has any non-zero contrast component (d64 [6][N]).
+cudaError_t launch_plane_active(const double* d64, long N, long nxy, int nz, int* act, cudaStream_t s);
 // Contraction form: M = 2 sigma0 (dsigma + 2 sigma0 I)^-1 and K = dsigma M from the FP64 contrast.
 cudaError_t launch_contract_tensors(const double* d64, long N, double sigma0, double* K64, double* M64, float* K32,
                                     float* M32, cudaStream_t s);

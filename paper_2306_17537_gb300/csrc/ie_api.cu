@@ -101,6 +101,9 @@ struct ie_ctx {
   DevBuf tw64, tw32, twdf;
   DevBuf ds64, ds32, s6_stage;
   DevBuf ck64, cm64, ck32, cm32;  // contraction form: K = dsigma M and M (built on first use)
+  DevBuf plane_act;               // per z plane: any non-zero contrast (device)
+  std::vector<char> active;       // the same on the host
+  std::vector<std::pair<int, int>> e_slabs;  // z ranges over which e is measured (empty: the whole grid)
   bool contract_ready = false;
   DevBuf cw32, cw64;             // w = M x of the contraction operator (block-local scratch)
   // GMRES as CUDA graphs: capture streams, device state, instantiated graphs (most recent last)
@@ -532,6 +535,20 @@ ie_status norm_c128(ie_ctx* c, const double2* a, long a_cs, const float2* b, lon
   return IE_OK;
 }
 
+// |a| over the z slabs of c->e_slabs (the whole grid when empty) for a whole-grid c128 field.
+ie_status slab_norm(ie_ctx* c, const double2* a, double* out) {
+  if (c->e_slabs.empty()) return norm_c128(c, a, c->N, nullptr, 0, c->N, out);
+  const long nxy = (long)c->nx * c->ny;
+  double sq = 0.0;
+  for (const auto& sl : c->e_slabs) {
+    double v;
+    CKS(norm_c128(c, a + (long)sl.first * nxy, c->N, nullptr, 0, (long)sl.second * nxy, &v));
+    sq += v * v;
+  }
+  *out = std::sqrt(sq);
+  return IE_OK;
+}
+
 struct GmresOut {
   int iters = 0, matvecs = 0, reorth = 0;
   double rel = 0;
@@ -709,7 +726,7 @@ ie_status full_residual(ie_ctx* c, double e0norm, double* e, bool fast = false) 
     CKS(conv<float>(c, S, E32, c->N, 0, c->nz, 0, c->nz, 0, EPI_RESID128, E32, c->N, nullptr, 0, c->R.as<double2>(),
                     c->N, c->E0.as<double2>(), c->N));
     double rn;
-    CKS(norm_c128(c, c->R.as<double2>(), c->N, nullptr, 0, c->N, &rn));
+    CKS(slab_norm(c, c->R.as<double2>(), &rn));
     *e = rn / e0norm;
     if (!std::isfinite(*e)) return fail(c, IE_ECUDA, "non-finite residual");
     if (*e > kFastResidualAbove) return IE_OK;
@@ -718,7 +735,7 @@ ie_status full_residual(ie_ctx* c, double e0norm, double* e, bool fast = false) 
   CKS(conv<df>(c, S, Ed, c->N, 0, c->nz, 0, c->nz, 0, EPI_RESID128, Ed, c->N, nullptr, 0, c->R.as<double2>(), c->N,
                c->E0.as<double2>(), c->N));
   double rn;
-  CKS(norm_c128(c, c->R.as<double2>(), c->N, nullptr, 0, c->N, &rn));
+  CKS(slab_norm(c, c->R.as<double2>(), &rn));
   *e = rn / e0norm;
   if (!std::isfinite(*e)) return fail(c, IE_ECUDA, "non-finite residual");
   return IE_OK;
@@ -966,10 +983,35 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
   const int M = (int)cfg.split.size() - 1;
   const bool warm = c->has_init;
   c->has_init = false;  // an initial guess serves one source
+  // Sub-domains without contrast are left out of the sweeps and e is measured over the anomalous
+  // ones (Section 3.1); their field is filled in from the final residual (E + R = E0 + G dsigma E).
+  std::vector<char> blk_active(M, 1);
+  c->e_slabs.clear();
+  if (cfg.dd_mode != IE_DD_NONE) {
+    for (int i = 0; i < M; ++i) {
+      char any = 0;
+      for (int z = cfg.split[i]; z < cfg.split[i + 1]; ++z) any |= c->active[z];
+      blk_active[i] = any;
+      if (any) {
+        if (!c->e_slabs.empty() && c->e_slabs.back().first + c->e_slabs.back().second == cfg.split[i])
+          c->e_slabs.back().second += cfg.split[i + 1] - cfg.split[i];
+        else
+          c->e_slabs.emplace_back(cfg.split[i], cfg.split[i + 1] - cfg.split[i]);
+      }
+    }
+    if (c->e_slabs.size() == 1 && c->e_slabs[0].first == 0 && c->e_slabs[0].second == c->nz) c->e_slabs.clear();
+    info->active_blocks += (int)std::count(blk_active.begin(), blk_active.end(), 1);
+    if (std::count(blk_active.begin(), blk_active.end(), 1) == 0) {  // no contrast anywhere: E = E0
+      CK(cudaMemcpyAsync(c->E.p, c->E0.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToDevice, s));
+      return IE_OK;
+    }
+  } else {
+    info->active_blocks += 1;
+  }
   CK(cudaMemcpyAsync(c->E.p, c->E0.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToDevice, s));
   double e0norm;
-  CKS(norm_c128(c, c->E0.as<double2>(), c->N, nullptr, 0, c->N, &e0norm));
-  if (e0norm == 0.0) return IE_OK;  // no incident field inside the grid: E = 0
+  CKS(slab_norm(c, c->E0.as<double2>(), &e0norm));
+  if (e0norm == 0.0) return IE_OK;  // no incident field in the anomalous region: E = E0 there
   double e;
   const bool fast_ok = cfg.precision == IE_PREC_MIXED;  // complex128 mode keeps every residual in FP64
   CKS(full_residual(c, e0norm, &e, fast_ok));
@@ -1017,6 +1059,7 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
     }
     CK(c->AEb.ensure(sizeof(float2) * tot));
     for (int i = 0; i < M; ++i) {
+      if (!blk_active[i]) continue;
       const long nb = ops[i].nb(), off = (long)ops[i].z0 * nxy;
       KL(IE_K_FIELD, 72.0 * nb,
          launch_c128_to_c64(c->E.as<double2>() + off, c->N, reinterpret_cast<float2*>(dx), nb, nb, s));
@@ -1028,6 +1071,7 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
   while (e > cfg.tol && sweeps < cfg.max_outer) {
     int sweep_its = 0;
     for (int i = 0; i < M; ++i) {
+      if (!blk_active[i]) continue;
       const BlockOp<T>& A = ops[i];
       const long nb = A.nb(), off = (long)A.z0 * nxy;
       double2* Ri = c->R.as<double2>() + off;
@@ -1082,6 +1126,7 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
         KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(reinterpret_cast<const double2*>(dx), nb, Ei, c->N, nb, s));
       if (cfg.dd_mode == IE_DD_GAUSS_SEIDEL) {
         for (int j = i + 1; j < M; ++j) {  // interaction update of the later blocks (eq. 21)
+          if (!blk_active[j]) continue;
           const BlockOp<T>& Bj = ops[j];
           CKS(conv<T>(c, Sfull, dx, nb, A.z0, A.nz, A.z0, Bj.nz, Bj.z0, EPI_ACCUM128, nullptr, 0, nullptr, 0,
                       c->R.as<double2>() + (long)Bj.z0 * nxy, c->N, nullptr, 0));
@@ -1097,6 +1142,11 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
   }
   info->outer_iters += sweeps;
   info->final_rel_residual = std::max(info->final_rel_residual, e);
+  for (int i = 0; i < M; ++i) {  // field of the sub-domains left out: E0 + G dsigma E = E + R
+    if (blk_active[i]) continue;
+    const long nb = ops[i].nb(), off = (long)ops[i].z0 * nxy;
+    KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(c->R.as<double2>() + off, c->N, c->E.as<double2>() + off, c->N, nb, s));
+  }
   if (e > cfg.tol) return IE_ENOCONV;
   return IE_OK;
 }
@@ -1252,6 +1302,14 @@ static ie_status set_contrast_dev_impl(ie_ctx* c, const double* s6_dev) {
     c->has_contrast = false;
     return fail(c, IE_EINVAL, "conductivity not finite or not positive definite");
   }
+  // planes with contrast (sub-domains without any are left out of the DD sweeps)
+  CK(c->plane_act.ensure(sizeof(int) * c->nz));
+  KL(IE_K_FIELD, 48.0 * c->N,
+     launch_plane_active(c->ds64.as<double>(), c->N, (long)c->nx * c->ny, c->nz, c->plane_act.as<int>(), c->stream));
+  std::vector<int> act(c->nz);
+  CK(cudaMemcpyAsync(act.data(), c->plane_act.p, sizeof(int) * c->nz, cudaMemcpyDeviceToHost, c->stream));
+  CK(sync(c));
+  c->active.assign(act.begin(), act.end());
   c->has_contrast = true;
   c->has_field = false;
   c->contract_ready = false;

@@ -54,7 +54,7 @@ class ie_info(ct.Structure):
                 ("residual_history", ct.c_double * IE_MAX_HISTORY),
                 ("sweep_gmres_iters", ct.c_int32 * IE_MAX_HISTORY), ("reorth_passes", ct.c_int32),
                 ("warm_start_used", ct.c_int32), ("cold_rel_residual", ct.c_double),
-                ("warm_rel_residual", ct.c_double)]
+                ("warm_rel_residual", ct.c_double), ("active_blocks", ct.c_int32)]
 
     def history(self):
         return list(self.residual_history[: self.n_history])

@@ -298,6 +298,33 @@ def config3_item(seed: int, position: int, freq: float, n_positions: int = 64, s
     return Workload(name, g, 0.1, freq, s6, src, rx, z_split=split, tol=1e-6, restart=40)
 
 
+def isolated_blocks(n: int = 128) -> Workload:
+    """The isolated sub-domains model of Section 3.1: an n^3 grid of 0.25 m cells (32 m for n = 128) in a
+    0.1 S/m background with two resistive (0.01 S/m) slabs of 30 x 30 x 7.5 m centred on the tool axis,
+    10 m apart along z; x-directed magnetic dipole at the origin, 24 kHz. Sub-domains along z: the two
+    anomalous slabs and the background around and between them (which the DD sweeps leave out).
+    Receivers at the slab centres, in the gap and beside it. ``n`` < 128 shrinks every length by n/128."""
+    h = 0.25
+    scale = n / 128.0
+    g = centred_grid(n, n, n, h)
+    s6 = np.zeros((n, n, n, 6))
+    s6[..., :3] = 0.1
+    half_xy = int(round(60 * scale))   # 30 m lateral extent = 120 cells at full size
+    thick = int(round(30 * scale))     # 7.5 m = 30 cells
+    gap = int(round(40 * scale))       # 10 m = 40 cells
+    z0 = n // 2 - gap // 2 - thick
+    z1 = n // 2 + gap // 2
+    c = n // 2
+    for za in (z0, z1):
+        s6[za:za + thick, c - half_xy:c + half_xy, c - half_xy:c + half_xy, :3] = 0.01
+    src = [Dipole((0.0, 0.0, 0.0), (1.0, 0.0, 0.0))]
+    zc = (z0 + thick / 2 - n / 2) * h
+    rx = np.array([[0.0, 0.0, zc], [0.0, 0.0, -zc], [2.0, 0.0, 0.0], [4.0, 1.0, 0.0]])
+    split = [0, z0, z0 + thick, z1, z1 + thick, n]
+    name = f"isolated sub-domains {n}^3 @{h} m, two 0.01 S/m slabs in 0.1 S/m, 24 kHz x-dipole"
+    return Workload(name, g, 0.1, 2.4e4, s6, src, rx, z_split=split, tol=1e-6, restart=10)
+
+
 def config4_item(seed: int, n: int = 64) -> Workload:
     """One training/evaluation sample of the learned warm start: a model of the 128x128x256 @0.25 m
     dipping-TI-plus-ellipsoids generator (the tool at the centre of the full model, 400 kHz, sigma0

@@ -40,3 +40,17 @@ def test_generators_are_seeded_and_physical():
     c1 = inputs.config1(0)
     assert c1.sigma6.shape == (16, 16, 16, 6) and np.all(c1.sigma6[..., 3:] == 0)
     assert np.all((c1.sigma6[..., 0] >= 0.01) & (c1.sigma6[..., 0] <= 10))
+
+
+def test_isolated_blocks_layout():
+    # Section 3.1: two anomalous slabs of 7.5 m (30 cells of 0.25 m) 10 m (40 cells) apart, 30 x 30 m wide
+    wl = inputs.isolated_blocks(128)
+    d = wl.sigma6.copy()
+    d[..., :3] -= wl.sigma0
+    planes = np.array([np.any(d[z] != 0) for z in range(128)])
+    zs = wl.z_split
+    assert zs == [0, 14, 44, 84, 114, 128]
+    assert planes[zs[1]:zs[2]].all() and planes[zs[3]:zs[4]].all()
+    assert not planes[:zs[1]].any() and not planes[zs[2]:zs[3]].any() and not planes[zs[4]:].any()
+    assert np.count_nonzero(d[zs[1], :, :, 0]) == 120 * 120
+    assert np.allclose(d[d != 0], 0.01 - 0.1)
