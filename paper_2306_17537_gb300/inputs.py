@@ -298,6 +298,52 @@ def config3_item(seed: int, position: int, freq: float, n_positions: int = 64, s
     return Workload(name, g, 0.1, freq, s6, src, rx, z_split=split, tol=1e-6, restart=40)
 
 
+def paper_logging_formation() -> Formation:
+    """The logging formation of Section 3.3 as its text describes it (its figure is not available): a
+    2.5-D stack (layer normal in the x-z plane, 3 deg dip) of anisotropic shale layers around isotropic
+    sand layers spanning the well's climb from z = 0 to 79 m, offset by a fault near x = 450 m, with the
+    sand perturbation sigma_u (1 + alpha exp(-|r - r_c| / gamma)) at r_c = (500, 0, 40) m, alpha = 4,
+    gamma = 50 m. Layer conductivities are fixed values in the ranges of that section."""
+    dip = np.deg2rad(3.0)
+    nrm = np.array([-np.sin(dip), 0.0, np.cos(dip)])
+    iface = np.array([-10.0, 6.0, 18.0, 30.0, 44.0, 58.0, 70.0, 86.0])
+    sand = np.array([False, True, False, True, False, True, False, True, False])
+    sh = np.array([1.2, 0.05, 0.8, 0.03, 1.5, 0.04, 1.0, 0.06, 0.9])
+    ratio = np.array([3.0, 1.0, 4.0, 1.0, 2.5, 1.0, 3.5, 1.0, 3.0])
+    fault_n = np.array([np.cos(np.deg2rad(70.0)), 0.0, np.sin(np.deg2rad(70.0))])
+    return Formation(nrm, iface, sh, sh / ratio, sand, np.array([450.0, 0.0, 40.0]), fault_n, 6.0,
+                     np.array([500.0, 0.0, 40.0]), 4.0, 50.0)
+
+
+PAPER_LOGGING_WINDOWS = {
+    1: ((256, 128, 128), [0, 128, 256]),                  # 32 x 32 x 64 m, two sub-domains
+    2: ((256, 256, 256), [32 * k for k in range(9)]),     # 64 x 64 x 64 m, eight sub-domains
+}
+
+
+def paper_logging_item(position: int, n_positions: int = 64, window: int = 1, scale: int = 1) -> Workload:
+    """One position of the logging simulation of Section 3.3: the well runs at 85 deg from (0, 0, 0) to
+    (900, 0, 78.74) m; a tool-aligned window (window 1: 128 x 128 x 256 cells, two sub-domains; window 2:
+    256^3 cells, eight) of 0.25 m cells centred on the transmitter; z-directed magnetic dipole at 24 kHz
+    with receivers 7, 15 and 30 m ahead on the tool axis; sigma0 = 0.1 S/m; GS-A to e = 1e-3."""
+    (nz, ny, nx), split = PAPER_LOGGING_WINDOWS[window]
+    nz, ny, nx = nz // scale, ny // scale, nx // scale
+    split = [v // scale for v in split]
+    g = centred_grid(nx, ny, nz, 0.25)
+    end = np.array([900.0, 0.0, 78.74])
+    d = end / np.linalg.norm(end)
+    ex = np.cross([0.0, 1.0, 0.0], d)
+    ex /= np.linalg.norm(ex)
+    ey = np.cross(d, ex)
+    rot = np.stack([ex, ey, d], axis=1)
+    pos = end * (position / max(n_positions - 1, 1))
+    s6 = window_sigma6(paper_logging_formation(), g, pos, rot)
+    src = [Dipole((0.0, 0.0, 0.0), (0.0, 0.0, 1.0))]
+    rx = np.array([[0.0, 0.0, 7.0], [0.0, 0.0, 15.0], [0.0, 0.0, 30.0]])
+    name = f"Section 3.3 logging, window {window} ({nx}x{ny}x{nz} @0.25 m), position {position}/{n_positions}, 24 kHz"
+    return Workload(name, g, 0.1, 2.4e4, s6, src, rx, z_split=split, tol=1e-3, restart=10)
+
+
 def isolated_blocks(n: int = 128) -> Workload:
     """The isolated sub-domains model of Section 3.1: an n^3 grid of 0.25 m cells (32 m for n = 128) in a
     0.1 S/m background with two resistive (0.01 S/m) slabs of 30 x 30 x 7.5 m centred on the tool axis,
