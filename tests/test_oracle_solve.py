@@ -182,3 +182,49 @@ def test_adaptive_tolerance_and_gs_vs_jacobi_qualitative():
     assert gs_a.converged and gs_f.converged and ja_a.converged
     assert gs_a.gmres_total < gs_f.gmres_total
     assert gs_a.outer_iters <= ja_a.outer_iters
+
+
+# ---------------------------------------------------------------- Krylov outer iteration over the DD sweep
+def _small_dd_case():
+    wl = inputs.config2(0, scale=16)  # 8 x 8 x 16 cells, two sub-domains
+    from oracle import operator as oop_
+
+    dsig = oop_.contrast(wl.sigma6, wl.sigma0)
+    E0 = solve.incident_field_on_grid(wl.grid, inputs.Dipole((0.1, 0.0, 0.0), (0.0, 0.0, 1.0)), wl.freq, wl.sigma0)
+    return wl, dsig, E0
+
+
+def test_fgmres_dd_reaches_the_lu_solution():
+    from oracle import dd as odd
+    from oracle import operator as oop_
+
+    wl, dsig, E0 = _small_dd_case()
+    A = oop_.dense_matrix(dsig, wl.grid.h, wl.freq, wl.sigma0)
+    E_lu = np.linalg.solve(A, E0.ravel()).reshape(E0.shape)
+    for mode in ("gs", "jacobi"):
+        E, info = odd.fgmres_dd(dsig, E0, wl.z_split, wl.grid.h, wl.freq, wl.sigma0, mode=mode, eps=1e-10,
+                                restart=10, inner_tol=0.1)
+        assert info.converged and info.residuals[-1] <= 1e-10
+        assert np.linalg.norm(E - E_lu) <= 1e-8 * np.linalg.norm(E_lu)
+
+
+def test_fgmres_dd_needs_fewer_sweeps_than_the_fixed_point_iteration():
+    from oracle import dd as odd
+
+    wl, dsig, E0 = _small_dd_case()
+    _, fp = odd.dd_solve(dsig, E0, wl.z_split, wl.grid.h, wl.freq, wl.sigma0, mode="jacobi", eps=1e-8,
+                         adaptive=False, fixed_tol=1e-10, restart=30, max_outer=200, max_inner=3000)
+    _, kr = odd.fgmres_dd(dsig, E0, wl.z_split, wl.grid.h, wl.freq, wl.sigma0, mode="jacobi", eps=1e-8,
+                          restart=30, inner_tol=1e-10, max_inner=3000)
+    assert fp.converged and kr.converged
+    assert kr.outer_iters < fp.outer_iters
+
+
+def test_fgmres_with_one_block_and_exact_inner_solves_takes_one_step():
+    # one sub-domain covering the grid: the preconditioner is the exact inverse
+    from oracle import dd as odd
+
+    wl, dsig, E0 = _small_dd_case()
+    E, info = odd.fgmres_dd(dsig, E0, [0, wl.grid.nz], wl.grid.h, wl.freq, wl.sigma0, eps=1e-9, restart=5,
+                            inner_tol=1e-13, max_inner=5000)
+    assert info.converged and info.outer_iters == 1
