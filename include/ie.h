@@ -85,6 +85,11 @@ typedef struct {
                              and restarts on the device, one host synchronisation per block solve;
                              per-kernel timing of ie_profile_enable then covers only the launches
                              outside the graph); 0 (default): host-driven Arnoldi loop */
+  int32_t outer_krylov;   /* 1: flexible GMRES(outer_restart) on the whole-grid system, preconditioned by
+                             one DD sweep (dd_mode) with block tolerance outer_inner_tol, instead of the
+                             fixed-point sweeps of Algorithm 1 (the paper's conclusion); 0 (default) */
+  int32_t outer_restart;  /* restart length of that outer iteration (default 10, at most 127) */
+  double outer_inner_tol; /* block tolerance inside its preconditioner sweeps (default 0.1) */
 } ie_opts;
 
 #define IE_MAX_HISTORY 128

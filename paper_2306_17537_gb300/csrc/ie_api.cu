@@ -120,6 +120,7 @@ struct ie_ctx {
   DevBuf E, E0, R;  // c128 whole-grid fields
   DevBuf Ec64;      // complex64 copy of E for the early, complex64 residuals
   DevBuf AEb;       // complex64 A_ii E_i of every block (block right-hand-side norms; see solve_one)
+  DevBuf FV, FZ, PR;  // outer flexible GMRES: Arnoldi basis, preconditioned vectors, sweep residual
   bool has_field = false;
   DevBuf Einit;           // initial guess for the next solve (ie_set_initial_field_dev)
   bool has_init = false;
@@ -972,8 +973,117 @@ struct SolveCfg {
   int dd_mode;
   std::vector<int> split;
   int restart, max_outer, max_inner, precision, adaptive, contraction, graph;
-  double fixed_tol, tol;
+  int outer_krylov, outer_restart;
+  double fixed_tol, tol, outer_inner_tol;
 };
+
+// Flexible GMRES on the whole-grid system (I - G dsigma) E = E0 (eq. 8) over the active sub-domains,
+// right-preconditioned by one sweep of Algorithm 1 started from zero (Krylov outer iteration in place of
+// the fixed-point sweeps, as the paper's conclusion proposes). The Arnoldi vectors are whole-grid
+// complex128 fields with the slabs of inactive sub-domains zeroed; the operator is applied with the
+// FP64-accurate (double-float) convolution; classical Gram-Schmidt with the DGKS second pass and FP64
+// Givens rotations on the host. Each outer step costs one sweep, one whole-grid application and the
+// orthogonalisation; the true residual is recomputed at every restart.
+template <typename T, class Sweep>
+ie_status fgmres_outer(ie_ctx* c, const SolveCfg& cfg, const std::vector<char>& act, Sweep& sweep, double e0norm,
+                       double* e, int* sweeps, ie_info* info, bool record, bool fast_ok) {
+  const long N3 = 3 * c->N, nxy = (long)c->nx * c->ny;
+  const int m = cfg.outer_restart;
+  if (m < 1 || m > 127) return fail(c, IE_EINVAL, "outer restart must be in [1, 127]");
+  cudaStream_t s = c->stream;
+  CKS(ensure_scalars(c));
+  SpecSet* S = nullptr;
+  CKS(get_spec(c, c->nz, &S));
+  CK(c->FV.ensure(sizeof(double2) * (size_t)(m + 1) * N3));
+  CK(c->FZ.ensure(sizeof(double2) * (size_t)m * N3));
+  CK(c->PR.ensure(sizeof(double2) * N3));
+  double2* V = c->FV.as<double2>();
+  double2* Z = c->FZ.as<double2>();
+  double2* PR = c->PR.as<double2>();
+  const RedScratch sc = scratch(c);
+  double2* dh = c->dh.as<double2>();
+  double2* dh2 = c->dh2.as<double2>();
+  double2* dn = c->dnrm.as<double2>();
+  int* flag = c->flag.as<int>();
+  auto mask = [&](double2* v) -> ie_status {  // zero the slabs of the sub-domains left out
+    for (size_t i = 0; i + 1 < cfg.split.size(); ++i) {
+      if (act[i]) continue;
+      const long off = (long)cfg.split[i] * nxy, nb = (long)(cfg.split[i + 1] - cfg.split[i]) * nxy;
+      for (int k = 0; k < 3; ++k) CK(cudaMemsetAsync(v + k * c->N + off, 0, sizeof(double2) * nb, s));
+    }
+    return IE_OK;
+  };
+  std::vector<std::complex<double>> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  auto Hij = [&](int i, int j) -> std::complex<double>& { return H[(size_t)i * m + j]; };
+  while (*e > cfg.tol && *sweeps < cfg.max_outer) {
+    CKS(mask(c->R.as<double2>()));
+    const double beta = *e * e0norm;  // |R| over the active slabs
+    KL(IE_K_KRYLOV_MISC, 32.0 * N3, Krylov<double>::scale(c->R.as<double2>(), V, N3, nullptr, 1.0 / beta, s));
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jd = 0;
+    for (int j = 0; j < m && *sweeps < cfg.max_outer; ++j) {
+      double2* vj = V + (size_t)j * N3;
+      double2* zj = Z + (size_t)j * N3;
+      double2* w = V + (size_t)(j + 1) * N3;
+      CK(cudaMemcpyAsync(PR, vj, sizeof(double2) * N3, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemsetAsync(zj, 0, sizeof(double2) * N3, s));
+      int its = 0;
+      CKS(sweep(PR, zj, cfg.outer_inner_tol, &its));
+      ++*sweeps;
+      CKS(conv<df>(c, S, zj, c->N, 0, c->nz, 0, c->nz, 0, EPI_APPLY, zj, c->N, w, c->N, nullptr, 0, nullptr, 0));
+      CKS(mask(w));
+      const int nv = j + 1;
+      const double ng = (nv + kDotGroup - 1) / kDotGroup;
+      KL(IE_K_DOTS, 16.0 * N3 * (nv + ng),
+         Krylov<double>::dots(V, N3, nv, w, N3, true, dh, nullptr, nullptr, sc, s));
+      KL(IE_K_UPDATE, 16.0 * N3 * (nv + 2),
+         Krylov<double>::update(V, N3, nv, dh, w, N3, dn, dh + nv, 0.5, flag, nullptr, sc, s));
+      KL(IE_K_DOTS, 0, Krylov<double>::dots(V, N3, nv, w, N3, false, dh2, dh, flag, sc, s));
+      KL(IE_K_UPDATE, 0, Krylov<double>::update(V, N3, nv, dh2, w, N3, dn, nullptr, 0.0, nullptr, flag, sc, s));
+      KL(IE_K_KRYLOV_MISC, 32.0 * N3, Krylov<double>::scale(w, w, N3, dn, 0.0, s));
+      CK(cudaMemcpyAsync(c->hpin, dh, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(c->hpin + nv, dn, sizeof(double2), cudaMemcpyDeviceToHost, s));
+      CK(sync(c));
+      for (int i = 0; i < nv; ++i) Hij(i, j) = std::complex<double>(c->hpin[i].x, c->hpin[i].y);
+      const double hn = std::sqrt(std::max(c->hpin[nv].x, 0.0));
+      Hij(j + 1, j) = hn;
+      for (int i = 0; i < j; ++i) {
+        const std::complex<double> t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -std::conj(sn[i]) * Hij(i, j) + std::conj(cs[i]) * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const std::complex<double> a = Hij(j, j), d = Hij(j + 1, j);
+      const double den = std::sqrt(std::norm(a) + std::norm(d));
+      cs[j] = den != 0.0 ? std::conj(a) / den : 1.0;
+      sn[j] = den != 0.0 ? std::conj(d) / den : 0.0;
+      Hij(j, j) = cs[j] * a + sn[j] * d;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -std::conj(sn[j]) * g[j];
+      g[j] = cs[j] * g[j];
+      jd = j + 1;
+      const double est = std::abs(g[j + 1]) / e0norm;
+      if (!std::isfinite(est)) return fail(c, IE_ECUDA, "outer GMRES produced a non-finite residual");
+      if (record && info->n_history < IE_MAX_HISTORY) {
+        info->sweep_gmres_iters[info->n_history - 1] = its;
+        info->residual_history[info->n_history++] = est;
+      }
+      if (est <= cfg.tol || hn == 0.0) break;
+    }
+    for (int i = jd - 1; i >= 0; --i) {  // back substitution
+      std::complex<double> acc = g[i];
+      for (int k = i + 1; k < jd; ++k) acc -= Hij(i, k) * y[k];
+      y[i] = acc / Hij(i, i);
+    }
+    for (int i = 0; i < jd; ++i) c->hpin[i] = make_double2(y[i].real(), y[i].imag());
+    CK(cudaMemcpyAsync(c->dy.as<double2>(), c->hpin, sizeof(double2) * jd, cudaMemcpyHostToDevice, s));
+    KL(IE_K_KRYLOV_MISC, 16.0 * N3 * (jd + 2),
+       Krylov<double>::combine(Z, N3, jd, c->dy.as<double2>(), c->E.as<double2>(), N3, s));
+    CKS(full_residual(c, e0norm, e, fast_ok && *e > kFastResidualAbove));
+  }
+  return IE_OK;
+}
 
 // Algorithm 1 (with FP64 refinement) for the source whose E0 is in c->E0; leaves E in c->E.
 template <typename T>
@@ -1066,39 +1176,46 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
       CKS(ops[i].apply_conv(dx, reinterpret_cast<C<T>*>(c->AEb.as<float2>() + ae_off[i])));
     }
   }
-  int sweeps = 0;
+  // One sweep of Algorithm 1 over the active blocks on the residual Rb, accumulating the corrections into
+  // Eb. precond_tol <= 0: the sweep of the fixed-point iteration (block tolerance e/10 relative to
+  // |b_i| = |R_i + A_ii E_i|). precond_tol > 0: a preconditioner application started from Eb = 0, so
+  // b_i = R_i and every block is solved to precond_tol.
   bool inner_ok = true;
-  while (e > cfg.tol && sweeps < cfg.max_outer) {
-    int sweep_its = 0;
+  auto sweep = [&](double2* Rb, double2* Eb, double precond_tol, int* sweep_its) -> ie_status {
+    const bool pre = precond_tol > 0;
     for (int i = 0; i < M; ++i) {
       if (!blk_active[i]) continue;
       const BlockOp<T>& A = ops[i];
       const long nb = A.nb(), off = (long)A.z0 * nxy;
-      double2* Ri = c->R.as<double2>() + off;
-      double2* Ei = c->E.as<double2>() + off;
+      double2* Ri = Rb + off;
+      double2* Ei = Eb + off;
       double rnorm;
       CKS(norm_c128(c, Ri, c->N, nullptr, 0, nb, &rnorm));
       if (rnorm == 0.0) continue;
       // block right-hand side norm |b_i| = |R_i + A_ii E_i| (eqs. 21/23)
-      double bnorm;
-      if (cfg.dd_mode == IE_DD_NONE) {
+      double bnorm = rnorm;
+      if (pre) {
+      } else if (cfg.dd_mode == IE_DD_NONE) {
         CKS(norm_c128(c, c->E0.as<double2>(), c->N, nullptr, 0, c->N, &bnorm));
+      } else if (keep_ae) {
+        CKS(norm_c128(c, Ri, c->N, c->AEb.as<float2>() + ae_off[i], nb, nb, &bnorm));
+      } else if (std::is_same<T, float>::value) {
+        KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(Ei, c->N, reinterpret_cast<float2*>(dx), nb, nb, s));
+        CKS(A.apply_conv(dx, t2));
+        CKS(norm_c128(c, Ri, c->N, reinterpret_cast<const float2*>(t2), nb, nb, &bnorm));
       } else {
-        if (keep_ae) {
-          CKS(norm_c128(c, Ri, c->N, c->AEb.as<float2>() + ae_off[i], nb, nb, &bnorm));
-        } else if (std::is_same<T, float>::value) {
-          KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(Ei, c->N, reinterpret_cast<float2*>(dx), nb, nb, s));
-          CKS(A.apply_conv(dx, t2));
-          CKS(norm_c128(c, Ri, c->N, reinterpret_cast<const float2*>(t2), nb, nb, &bnorm));
-        } else {
-          KL(IE_K_FIELD, 96.0 * nb, launch_copy_c128(Ei, c->N, reinterpret_cast<double2*>(dx), nb, nb, s));
-          CKS(A.apply_conv(dx, t2));
-          KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(Ri, c->N, reinterpret_cast<double2*>(t2), nb, nb, s));
-          CKS(norm_c128(c, reinterpret_cast<const double2*>(t2), nb, nullptr, 0, nb, &bnorm));
-        }
+        KL(IE_K_FIELD, 96.0 * nb, launch_copy_c128(Ei, c->N, reinterpret_cast<double2*>(dx), nb, nb, s));
+        CKS(A.apply_conv(dx, t2));
+        KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(Ri, c->N, reinterpret_cast<double2*>(t2), nb, nb, s));
+        CKS(norm_c128(c, reinterpret_cast<const double2*>(t2), nb, nullptr, 0, nb, &bnorm));
       }
-      double target = (cfg.dd_mode == IE_DD_NONE) ? cfg.tol : (cfg.adaptive ? e / 10.0 : cfg.fixed_tol);
-      double tol_i = target * bnorm / rnorm;
+      double tol_i;
+      if (pre) {
+        tol_i = precond_tol;
+      } else {
+        const double target = (cfg.dd_mode == IE_DD_NONE) ? cfg.tol : (cfg.adaptive ? e / 10.0 : cfg.fixed_tol);
+        tol_i = target * bnorm / rnorm;
+      }
       if (std::is_same<T, float>::value) tol_i = std::max(tol_i, cfg.dd_mode == IE_DD_NONE ? 1e-5 : 1e-6);
       tol_i = std::min(tol_i, 0.5);
       if (std::is_same<T, float>::value)
@@ -1110,13 +1227,13 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
         CKS(gmres_graph<T>(c, A, rhs, dx, tol_i, cfg.restart, cfg.max_inner, &go));
       else
         CKS(gmres<T>(c, A, rhs, dx, true, tol_i, cfg.restart, cfg.max_inner, &go));
-      if (keep_ae && go.iters > 0)  // A_ii delta = rhs - r with r = rhs - A x the final true residual (kt1)
+      if (keep_ae && !pre && go.iters > 0)  // A_ii delta = rhs - r, r = rhs - A x the final true residual
         KL(IE_K_FIELD, 96.0 * nb,
            launch_add_diff_c64(c->AEb.as<float2>() + ae_off[i], reinterpret_cast<const float2*>(rhs),
                                c->kt1.as<float2>(), 3 * nb, s));
       CKS(A.to_field(dx));  // contraction form: the field correction is M times the GMRES solution
       inner_ok = inner_ok && go.converged;
-      sweep_its += go.iters;
+      *sweep_its += go.iters;
       info->gmres_iters_total += go.iters;
       info->reorth_passes += go.reorth;
       info->matvecs += go.matvecs;
@@ -1129,15 +1246,25 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
           if (!blk_active[j]) continue;
           const BlockOp<T>& Bj = ops[j];
           CKS(conv<T>(c, Sfull, dx, nb, A.z0, A.nz, A.z0, Bj.nz, Bj.z0, EPI_ACCUM128, nullptr, 0, nullptr, 0,
-                      c->R.as<double2>() + (long)Bj.z0 * nxy, c->N, nullptr, 0));
+                      Rb + (long)Bj.z0 * nxy, c->N, nullptr, 0));
         }
       }
     }
-    sweeps++;
-    CKS(full_residual(c, e0norm, &e, fast_ok && e > kFastResidualAbove));
-    if (record && info->n_history < IE_MAX_HISTORY) {
-      info->sweep_gmres_iters[info->n_history - 1] = sweep_its;
-      info->residual_history[info->n_history++] = e;
+    return IE_OK;
+  };
+  int sweeps = 0;
+  if (cfg.outer_krylov && cfg.dd_mode != IE_DD_NONE) {
+    CKS(fgmres_outer<T>(c, cfg, blk_active, sweep, e0norm, &e, &sweeps, info, record, fast_ok));
+  } else {
+    while (e > cfg.tol && sweeps < cfg.max_outer) {
+      int sweep_its = 0;
+      CKS(sweep(c->R.as<double2>(), c->E.as<double2>(), 0.0, &sweep_its));
+      sweeps++;
+      CKS(full_residual(c, e0norm, &e, fast_ok && e > kFastResidualAbove));
+      if (record && info->n_history < IE_MAX_HISTORY) {
+        info->sweep_gmres_iters[info->n_history - 1] = sweep_its;
+        info->residual_history[info->n_history++] = e;
+      }
     }
   }
   info->outer_iters += sweeps;
@@ -1352,6 +1479,10 @@ ie_status ie_solve(ie_ctx* c, int32_t n_src, const ie_dipole* src, int32_t n_rx,
   cfg.tol = tol;
   cfg.contraction = o.contraction;
   cfg.graph = o.graph;
+  cfg.outer_krylov = o.outer_krylov;
+  cfg.outer_restart = o.outer_restart > 0 ? o.outer_restart : 10;
+  cfg.outer_inner_tol = o.outer_inner_tol > 0 ? o.outer_inner_tol : 0.1;
+  if (o.outer_krylov != 0 && o.outer_krylov != 1) return fail(c, IE_EINVAL, "outer_krylov must be 0 or 1");
   if (o.graph != 0 && o.graph != 1) return fail(c, IE_EINVAL, "graph must be 0 or 1");
   if (o.contraction != 0 && o.contraction != 1) return fail(c, IE_EINVAL, "contraction must be 0 or 1");
   if (cfg.precision != IE_PREC_MIXED && cfg.precision != IE_PREC_FP64) return fail(c, IE_EINVAL, "bad precision");

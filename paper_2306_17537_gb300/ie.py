@@ -38,7 +38,8 @@ class ie_opts(ct.Structure):
     _fields_ = [("n_blocks", ct.c_int32), ("z_split", ct.POINTER(ct.c_int32)), ("restart", ct.c_int32),
                 ("max_outer", ct.c_int32), ("max_inner", ct.c_int32), ("precision", ct.c_int32),
                 ("adaptive", ct.c_int32), ("fixed_tol", ct.c_double), ("contraction", ct.c_int32),
-                ("graph", ct.c_int32)]
+                ("graph", ct.c_int32), ("outer_krylov", ct.c_int32), ("outer_restart", ct.c_int32),
+                ("outer_inner_tol", ct.c_double)]
 
 
 class ie_batch_item(ct.Structure):
@@ -453,7 +454,8 @@ def tuned_tiles() -> str:
 
 
 def make_opts(n_blocks=1, z_split=None, restart=30, max_outer=50, max_inner=600, precision=IE_PREC_MIXED,
-              adaptive=True, fixed_tol=1e-6, contraction=False, graph=False) -> ie_opts:
+              adaptive=True, fixed_tol=1e-6, contraction=False, graph=False, outer_krylov=False, outer_restart=10,
+              outer_inner_tol=0.1) -> ie_opts:
     o = ie_default_opts()
     o.n_blocks = int(n_blocks)
     if z_split is not None:
@@ -465,6 +467,7 @@ def make_opts(n_blocks=1, z_split=None, restart=30, max_outer=50, max_inner=600,
     o.precision, o.adaptive, o.fixed_tol = int(precision), int(bool(adaptive)), float(fixed_tol)
     o.contraction = int(bool(contraction))
     o.graph = int(bool(graph))
+    o.outer_krylov, o.outer_restart, o.outer_inner_tol = int(bool(outer_krylov)), int(outer_restart), float(outer_inner_tol)
     return o
 
 
