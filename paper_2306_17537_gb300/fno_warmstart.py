@@ -69,8 +69,8 @@ class Data:
         self.ok = np.zeros(count, dtype=bool)
 
 
-def solve_opts(ie, restart, max_inner, max_outer):
-    return ie.make_opts(restart=restart, max_inner=max_inner, max_outer=max_outer)
+def solve_opts(ie, restart, max_inner, max_outer, contraction=False):
+    return ie.make_opts(restart=restart, max_inner=max_inner, max_outer=max_outer, contraction=contraction)
 
 
 def generate(torch, ie, net, ctx, wl0, models, data, tol, opts):
@@ -206,7 +206,7 @@ def init_flat(ie, n, modes, width, layers, hidden, seed):
 
 
 def run(n=64, n_train=1800, n_test=200, epochs=30, batch=8, lr=2e-3, modes=12, width=32, layers=4, hidden=128,
-        tol=1e-6, restart=40, max_inner=8000, max_outer=6, workers=8, seed0=0, log=None):
+        tol=1e-6, restart=40, max_inner=8000, max_outer=6, workers=8, seed0=0, log=None, contraction=False):
     import torch
 
     from . import ie, inputs
@@ -216,8 +216,9 @@ def run(n=64, n_train=1800, n_test=200, epochs=30, batch=8, lr=2e-3, modes=12, w
     res = {"n": n, "train": n_train, "test": n_test, "epochs": epochs, "batch": batch, "lr": lr,
            "net": {"modes": modes, "width": width, "layers": layers, "hidden": hidden, "storage": "bf16"},
            "solver": {"tol": tol, "restart": restart, "max_inner": max_inner, "max_outer": max_outer,
-                      "precision": "mixed (complex64 GMRES, FP64-accurate residual)"}}
-    opts_of = lambda: solve_opts(ie, restart, max_inner, max_outer)  # noqa: E731
+                      "precision": "mixed (complex64 GMRES, FP64-accurate residual)",
+                      "operator": "contraction" if contraction else "conventional"}}
+    opts_of = lambda: solve_opts(ie, restart, max_inner, max_outer, contraction)  # noqa: E731
     with ie.Context(wl0.grid, wl0.grid.h, wl0.sigma0, wl0.freq) as ctx, \
             ie.FNO(n, modes=modes, width=width, layers=layers, hidden=hidden, batch_max=batch, bf16=True) as net:
         net.set_params(init_flat(ie, n, modes, width, layers, hidden, seed0))
@@ -260,10 +261,12 @@ def main(argv=None):
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--max-inner", type=int, default=8000)
     ap.add_argument("--max-outer", type=int, default=6)
+    ap.add_argument("--contraction", action="store_true", help="block solves on the contraction form")
     ap.add_argument("--full-lists", action="store_true", help="keep per-solve iteration lists in the output")
     a = ap.parse_args(argv)
     res = run(a.n, a.train, a.test, a.epochs, a.batch, a.lr, a.modes, a.width, a.layers, a.hidden,
-              max_inner=a.max_inner, max_outer=a.max_outer, workers=a.workers, log=lambda s: print(s, flush=True))
+              max_inner=a.max_inner, max_outer=a.max_outer, workers=a.workers, log=lambda s: print(s, flush=True),
+              contraction=a.contraction)
     if not a.full_lists:
         for k in ("cold", "warm"):
             for key in ("iters", "matvecs", "initial_e_cold", "initial_e_warm"):
