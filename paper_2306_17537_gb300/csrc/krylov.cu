@@ -3,9 +3,9 @@
 //
 // Vectors are complex64 (mixed precision) or complex128, 16-byte aligned, read as 16-byte packets
 // (two complex64 or one complex128 values). Every inner product and norm is reduced in FP64 across
-// threads and blocks. Within a thread the complex64 products are summed in FP32 with Kahan
-// compensation, so the accumulated rounding stays at the level of the FP32 products themselves
-// while the FP64 pipe (a small fraction of the FP32 rate on this part) is only used once per thread.
+// threads and blocks. Within a thread the complex64 products (a few dozen at most, see krylov_blocks)
+// are summed in FP32, across the lanes of a warp in double-float, and the FP64 pipe (a small
+// fraction of the FP32 rate on this part) is only used once per warp.
 // Each reduction finishes in the last block to arrive (partials summed in a fixed order, so the
 // result is deterministic); no separate reduction launch is needed.
 #include "green.cuh"
@@ -40,19 +40,18 @@ template <> struct Pk<double> {
 };
 
 template <typename T> struct Acc;  // per-thread complex accumulator
-template <> struct Acc<float> {    // Kahan-compensated FP32
-  float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+// FP32 per thread: a thread sums at most a few dozen products (the grids are sized to keep it so:
+// krylov_blocks), so its rounding stays at a few units of FP32 epsilon relative to the partial sum;
+// the sums across threads, where the count grows with n, are carried in double-float and FP64.
+template <> struct Acc<float> {
+  float2 s = make_float2(0.f, 0.f);
   __device__ __forceinline__ void add(float2 x) {
-    float yr = x.x - c.x, tr = s.x + yr;
-    c.x = (tr - s.x) - yr;
-    s.x = tr;
-    float yi = x.y - c.y, ti = s.y + yi;
-    c.y = (ti - s.y) - yi;
-    s.y = ti;
+    s.x += x.x;
+    s.y += x.y;
   }
-  // Sum over the warp in double-float (FP32 pipes; compensation kept), converted to FP64 once.
+  // Sum over the warp in double-float (FP32 pipes), converted to FP64 once.
   __device__ __forceinline__ double2 warp_total() const {
-    df re(s.x, -c.x), im(s.y, -c.y);
+    df re(s.x, 0.f), im(s.y, 0.f);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const df r2(__shfl_down_sync(0xffffffffu, re.hi, o), __shfl_down_sync(0xffffffffu, re.lo, o));
