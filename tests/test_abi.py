@@ -57,3 +57,50 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib_path):
         st = ie._lib.ie_create(ctypes.byref(g), h, s0, f, ctypes.byref(p))
         assert st == ie.IE_EINVAL and not p.value
     assert ie._lib.ie_last_error(None) == b"null context"
+
+
+def _c_layout(structs):
+    """sizeof and offsetof of each struct field as the C compiler lays out include/ie.h (gcc, host)."""
+    import shutil
+    import subprocess
+    import tempfile
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ie.h"', "int main(void) {"]
+    for st, fields in structs.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fields:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    res = {}
+    for line in out.splitlines():
+        st, key, val = line.split()
+        res[(st, key)] = int(val)
+    return res
+
+
+def test_binding_structs_match_the_header_layout():
+    """The ctypes mirrors of ie_grid, ie_dipole, ie_opts, ie_info and ie_batch_item have the sizes and field
+    offsets the C compiler gives the header's structs (a field added on one side only fails here)."""
+    from paper_2306_17537_gb300 import build
+
+    if not os.path.exists(build.LIB):
+        pytest.skip("library not built")
+    from paper_2306_17537_gb300 import ie
+
+    mirrors = {"ie_grid": ie.ie_grid, "ie_dipole": ie.ie_dipole, "ie_opts": ie.ie_opts, "ie_info": ie.ie_info,
+               "ie_batch_item": ie.ie_batch_item}
+    structs = {name: [f[0] for f in cls._fields_] for name, cls in mirrors.items()}
+    c = _c_layout(structs)
+    for name, cls in mirrors.items():
+        assert ctypes.sizeof(cls) == c[(name, "size")], name
+        for fname in structs[name]:
+            assert getattr(cls, fname).offset == c[(name, fname)], (name, fname)
