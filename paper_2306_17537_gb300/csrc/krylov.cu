@@ -8,6 +8,8 @@
 // fraction of the FP32 rate on this part) is only used once per warp.
 // Each reduction finishes in the last block to arrive (partials summed in a fixed order, so the
 // result is deterministic); no separate reduction launch is needed.
+#include <algorithm>
+
 #include "green.cuh"
 
 namespace ie {
@@ -383,7 +385,18 @@ template <typename T>
 cudaError_t Krylov<T>::dots(const C<T>* V, long ld, int nv, const C<T>* w, long n, bool with_norm, double2* out,
                             double2* acc, const int* skip, const RedScratch& sc, cudaStream_t s) {
   if (nv < 1 || nv > kMaxBasis) return cudaErrorInvalidValue;
-  dim3 grd(krylov_blocks(n), (nv + kDotGroup - 1) / kDotGroup);
+  // blocks the GPU holds at once for this kernel: the groups' blocks together fill one wave
+  static const int resident = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dots<T>, kKThreads, 0);
+    cudaGetLastError();
+    return sms * per_sm > 0 ? sms * per_sm : kRedBlocks;
+  }();
+  const int ng = (nv + kDotGroup - 1) / kDotGroup;
+  const int gx = std::max(1, std::min(krylov_blocks(n), resident / ng));
+  dim3 grd(gx, ng);
   k_dots<T><<<grd, kKThreads, 0, s>>>(V, ld, nv, w, n, with_norm ? 1 : 0, sc.part, sc.counters, out, acc, skip);
   return cudaGetLastError();
 }
