@@ -64,3 +64,25 @@ def test_no_contrast_anywhere_returns_the_incident_field(ie):
         E0 = ctx.incident_field(wl.sources[0])
     assert st == ie.IE_OK and info.active_blocks == 0 and info.gmres_iters_total == 0
     assert np.array_equal(E, E0)
+
+
+def test_isolated_sub_domains_example_reproduces_the_papers_counts(ie):
+    # Section 3.1 prints the outcome of this fully specified example: the IE-DD Gauss-Seidel iteration
+    # (GMRES(10), block tolerance fixed at 1e-6, background sub-domains excluded) converges in four
+    # sweeps with 278 GMRES iterations in total, and the full-domain IE takes 86 iterations. The sweep
+    # count is reproduced exactly; the iteration totals depend on discretisation details the paper does
+    # not give (self term, source placement), so they are checked to the same order.
+    wl = inputs.isolated_blocks(128)
+    with ie.Context(wl.grid, wl.grid.h, wl.sigma0, wl.freq) as ctx:
+        ctx.set_contrast(wl.sigma6)
+        opts = ie.make_opts(z_split=wl.z_split, restart=10, max_inner=4000, max_outer=40, adaptive=False,
+                            fixed_tol=1e-6)
+        H, info, st = ctx.solve(wl.sources, wl.receivers, ie.IE_DD_GAUSS_SEIDEL, 1e-6, opts)
+        full = ie.make_opts(restart=10, max_inner=4000, max_outer=20)
+        Hf, infof, stf = ctx.solve(wl.sources, wl.receivers, ie.IE_DD_NONE, 1e-6, full)
+    assert st == stf == ie.IE_OK
+    assert info.outer_iters == 4
+    assert 0.5 * 278 <= info.gmres_iters_total <= 1.5 * 278
+    assert infof.gmres_iters_total <= 2 * 86
+    # "less than 0.01 per cent average normalized magnitude difference" between the two
+    assert np.mean(np.abs(np.abs(H) - np.abs(Hf)) / np.max(np.abs(Hf))) <= 1e-4
