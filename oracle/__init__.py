@@ -17,9 +17,15 @@ decomposition preconditioning"):
                operator with 2x zero padding, dense matrix for tiny grids.
   gmres.py     restarted GMRES (Saad & Schultz) with the relative-residual rule of eq. 9.
   dd.py        Section 2.3, eqs. 11-23 and Algorithm 1: block Gauss-Seidel / block Jacobi sweeps
-               with adaptive sub-domain tolerance and warm starts.
+               with adaptive sub-domain tolerance and warm starts; flexible GMRES over one sweep
+               (the Krylov outer iteration of the paper's conclusion).
   solve.py     the full forward model: incident field, solve, receiver fields.
+  contraction.py  the contraction form of the operator (named at the end of Section 2.3).
+  fno.py       the warm-start network (not in the paper): forward and analytic backward.
 
 Readings where the paper is silent or garbled are marked "Reading:" in the docstrings.
-Every function here is pinned by the ``-m "not gpu"`` tests; none is "parity unpinned".
+Every function here is pinned by the ``-m "not gpu"`` tests against closed forms, finite differences,
+brute force or the LU solution. The contraction form is parity unpinned against the paper itself
+(the paper prints no formula for it); it is pinned by its equivalence with the conventional solution
+and by the contraction property of the discrete operator.
 """
