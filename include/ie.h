@@ -94,13 +94,16 @@ typedef struct {
 
 #define IE_MAX_HISTORY 128
 typedef struct {
-  int32_t outer_iters;       /* DD sweeps (or refinement steps) performed, summed over sources */
+  int32_t outer_iters;       /* DD sweeps (or refinement steps; with outer_krylov the preconditioner
+                                sweeps) performed, summed over sources */
   int32_t gmres_iters_total; /* Arnoldi steps over all block solves and sources */
   int32_t matvecs;           /* block operator applications (Arnoldi + restart residuals) */
   int32_t n_history;         /* entries used in residual_history (first source only) */
-  double final_rel_residual; /* max over sources of the FP64 whole-domain e (eq. 9) at exit */
+  double final_rel_residual; /* max over sources of the FP64-accurate e (eq. 9) at exit, measured over
+                                the sub-domains with contrast (the whole grid when all have some) */
   double seconds;            /* wall time of the call */
-  double residual_history[IE_MAX_HISTORY]; /* e before the first sweep and after each sweep */
+  double residual_history[IE_MAX_HISTORY]; /* e before the first sweep and after each sweep (with
+                                              outer_krylov: the outer GMRES estimate after each step) */
   int32_t sweep_gmres_iters[IE_MAX_HISTORY]; /* GMRES iterations per sweep (first source) */
   int32_t reorth_passes;     /* Arnoldi steps that needed a second Gram-Schmidt pass */
   int32_t warm_start_used;   /* 1 if the guess of ie_set_initial_field_dev replaced E := E0 */
