@@ -163,6 +163,8 @@ typedef struct {
   double* H_out;           /* [n_src][n_rx][3] complex */
   ie_info* info;           /* may be NULL */
   ie_status status;        /* result of this item */
+  const double* E_init_dev; /* may be NULL: initial guess for this item's first source, as for
+                               ie_set_initial_field_dev (device complex128 [3][nz][ny][nx]) */
 } ie_batch_item;
 
 /* Many independent forward problems (tool positions x frequencies, Section 3.3's moving window) in

@@ -1580,6 +1580,7 @@ ie_status ie_solve_batch(int32_t n_items, ie_batch_item* items, int32_t max_conc
       for (int i : groups[g]) {
         ie_batch_item& it = items[i];
         it.status = it.sigma6 ? ie_set_contrast(it.ctx, it.sigma6) : IE_OK;
+        if (it.status == IE_OK && it.E_init_dev) it.status = ie_set_initial_field_dev(it.ctx, it.E_init_dev);
         if (it.status == IE_OK)
           it.status = ie_solve(it.ctx, it.n_src, it.src, it.n_rx, it.rx_xyz, it.dd_mode, it.tol, it.opts, it.H_out,
                                it.info);

@@ -46,7 +46,8 @@ class ie_batch_item(ct.Structure):
     _fields_ = [("ctx", ct.c_void_p), ("sigma6", ct.POINTER(ct.c_double)), ("n_src", ct.c_int32),
                 ("src", ct.POINTER(ie_dipole)), ("n_rx", ct.c_int32), ("rx_xyz", ct.POINTER(ct.c_double)),
                 ("dd_mode", ct.c_int32), ("tol", ct.c_double), ("opts", ct.POINTER(ie_opts)),
-                ("H_out", ct.POINTER(ct.c_double)), ("info", ct.c_void_p), ("status", ct.c_int)]
+                ("H_out", ct.POINTER(ct.c_double)), ("info", ct.c_void_p), ("status", ct.c_int),
+                ("E_init_dev", ct.c_void_p)]
 
 
 class ie_info(ct.Structure):
@@ -322,7 +323,8 @@ class Context:
 
 def solve_batch(problems, max_concurrent=0):
     """ie_solve_batch on a list of dicts with keys ctx (Context), sources, receivers and optionally
-    sigma6 (host array set on the context before that item), dd_mode, tol, opts. Items sharing a
+    sigma6 (host array set on the context before that item), dd_mode, tol, opts, E_init_dev (device
+    complex128 initial guess, see Context.set_initial_field_dev). Items sharing a
     context run in order; different contexts run concurrently. Returns [(H, info, status)]."""
     n = len(problems)
     items = (ie_batch_item * max(1, n))()
@@ -345,6 +347,8 @@ def solve_batch(problems, max_concurrent=0):
         it.opts = ct.pointer(o) if o is not None else None
         it.H_out = _dptr(H)
         it.info = ct.cast(ct.pointer(info), ct.c_void_p)
+        init = p.get("E_init_dev")
+        it.E_init_dev = _addr(init) if init is not None else None
         keep += [src, rx, s6, o, info]
         outs.append((H, info))
     _lib.ie_solve_batch(n, items, int(max_concurrent))

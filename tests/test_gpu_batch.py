@@ -58,3 +58,26 @@ def test_batch_result_checked_by_oracle(ie):
     ref = osolve.receiver_fields(w.grid, oop.contrast(w.sigma6, w.sigma0), E, w.sources[0], w.receivers, w.freq,
                                  w.sigma0)
     assert np.max(np.abs(H[0] - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_batch_item_initial_guess():
+    # an item carrying its converged field as the initial guess needs no iterations; one without is cold
+    import torch
+
+    from paper_2306_17537_gb300 import ie
+
+    wl = inputs.config4_item(0, 32)
+    n3 = wl.grid.n
+    with ie.Context(wl.grid, wl.grid.h, wl.sigma0, wl.freq) as c1, ie.Context(wl.grid, wl.grid.h, wl.sigma0, wl.freq) as c2:
+        o = ie.make_opts(restart=40, max_inner=4000, max_outer=4)
+        c1.set_contrast(wl.sigma6)
+        _, i0, _ = c1.solve(wl.sources, [], ie.IE_DD_NONE, 1e-6, o)
+        E = torch.empty((3, n3), dtype=torch.complex128, device=torch.device("cuda", 0))
+        c1.get_field_dev(E)
+        torch.cuda.synchronize()
+        res = ie.solve_batch([dict(ctx=c1, sigma6=wl.sigma6, sources=wl.sources, receivers=[], tol=1e-6, opts=o, E_init_dev=E),
+                              dict(ctx=c2, sigma6=wl.sigma6, sources=wl.sources, receivers=[], tol=1e-6, opts=o)])
+    (_, warm, sw), (_, cold, sc) = res
+    assert sw == sc == ie.IE_OK
+    assert warm.warm_start_used == 1 and warm.gmres_iters_total == 0
+    assert cold.warm_start_used == 0 and cold.gmres_iters_total == i0.gmres_iters_total
