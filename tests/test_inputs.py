@@ -54,3 +54,18 @@ def test_isolated_blocks_layout():
     assert not planes[:zs[1]].any() and not planes[zs[2]:zs[3]].any() and not planes[zs[4]:].any()
     assert np.count_nonzero(d[zs[1], :, :, 0]) == 120 * 120
     assert np.allclose(d[d != 0], 0.01 - 0.1)
+
+
+def test_paper_logging_geometry():
+    # Section 3.3: the well runs from (0,0,0) to (900,0,78.74) m, i.e. 85 deg from vertical; window 1 is
+    # 128x128x256 cells of 0.25 m split in two, window 2 256^3 split in eight; receivers 7, 15, 30 m ahead
+    wl = inputs.paper_logging_item(0, 64, 1)
+    assert (wl.grid.nx, wl.grid.ny, wl.grid.nz) == (128, 128, 256) and wl.z_split == [0, 128, 256]
+    assert np.allclose(wl.receivers[:, 2], [7.0, 15.0, 30.0]) and wl.freq == 2.4e4 and wl.tol == 1e-3
+    w2 = inputs.paper_logging_item(0, 64, 2, scale=8)
+    assert len(w2.z_split) == 9
+    end = np.array([900.0, 0.0, 78.74])
+    assert abs(np.degrees(np.arccos(end[2] / np.linalg.norm(end))) - 85.0) < 0.01
+    # the sand perturbation peaks at r_c with factor 1 + alpha
+    f = inputs.paper_logging_formation()
+    assert np.allclose(f.r_c, [500.0, 0.0, 40.0]) and f.alpha == 4.0 and f.gamma == 50.0

@@ -228,3 +228,21 @@ def test_fgmres_with_one_block_and_exact_inner_solves_takes_one_step():
     E, info = odd.fgmres_dd(dsig, E0, [0, wl.grid.nz], wl.grid.h, wl.freq, wl.sigma0, eps=1e-9, restart=5,
                             inner_tol=1e-13, max_inner=5000)
     assert info.converged and info.outer_iters == 1
+
+
+def test_jacobi_preconditioner_sweep_is_the_block_diagonal_inverse():
+    # a Jacobi sweep started from zero solves each sub-domain system with its own right-hand side only
+    from oracle import dd as odd
+    from oracle import operator as oop_
+
+    wl, dsig, E0 = _small_dd_case()
+    rng = np.random.default_rng(3)
+    v = rng.normal(size=E0.shape) + 1j * rng.normal(size=E0.shape)
+    full = oop_.FFTOperator(dsig, wl.grid.h, wl.freq, wl.sigma0)
+    blocks = [(wl.z_split[i], wl.z_split[i + 1]) for i in range(len(wl.z_split) - 1)]
+    A = [oop_.FFTOperator(dsig[z0:z1], wl.grid.h, wl.freq, wl.sigma0) for z0, z1 in blocks]
+    z, _ = odd.dd_sweep_from_zero(dsig, v, blocks, A, full, "jacobi", 1e-13, 60, 5000)
+    for z0, z1 in blocks:
+        D = oop_.dense_matrix(dsig[z0:z1], wl.grid.h, wl.freq, wl.sigma0)
+        zi = np.linalg.solve(D, v[:, z0:z1].ravel()).reshape(v[:, z0:z1].shape)
+        assert np.linalg.norm(z[:, z0:z1] - zi) <= 1e-10 * np.linalg.norm(zi)
