@@ -131,7 +131,7 @@ cudaError_t ConvLaunch<T>::lanes(int L, int sign, int variant, const C<T>* in, l
   }
 }
 
-// cuTensorMapEncodeTiled from the driver, looked up once (null when the driver does not provide it).
+// cuTensorMapEncodeTiled from the CUDA driver, looked up once (null when the CUDA driver lacks it).
 inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -147,7 +147,7 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // TMA = true stages the input pencils with tensor copies when the tile allows it (P3Cfg::kTmaOk) and
-// the driver provides the tensor-map encoder; otherwise the same tile runs with register loads.
+// the CUDA driver provides the tensor-map encoder; otherwise the same tile runs with register loads.
 template <typename T, int N, int WDIV, bool TMA>
 static cudaError_t p3_launch(const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt, int ot,
                              const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err, cudaStream_t s) {
