@@ -210,18 +210,25 @@ ie_status ie_matvec(ie_ctx* ctx, int32_t precision, int32_t z0, int32_t nz, cons
  * enqueued on the context stream without synchronising. */
 ie_status ie_matvec_dev(ie_ctx* ctx, int32_t z0, int32_t nz, const void* x_dev, void* y_dev);
 
-/* Same operator as ie_matvec_dev, for callers that must not allocate device memory during the call:
- * code running while a CUDA stream is being captured, real-time loops with a fixed memory budget, or
- * hosts whose allocator is owned by someone else. (An extension of this library; the paper has no
- * counterpart.) The FFT intermediates go to one fixed 16 MiB device array that the library reserves
- * on every GPU it is loaded on; slabs needing more (24 * nz * Lx * (ny + Ly) bytes, Lx/Ly the padded
- * FFT lengths) are rejected with IE_EINVAL. The Green spectra for the slab height must already exist
- * (ie_create prepares the whole grid; otherwise call ie_matvec_dev once first), else IE_ESTATE.
- * The first call on each device looks up the array's device address; make that call before any
- * stream capture. All calls share the array: calls that overlap on the GPU (different streams or
- * contexts at the same time) race and give wrong results. Nothing in it needs clearing between
- * calls. x_dev, y_dev: distinct device arrays [3][nz][ny][nx] complex64; work is enqueued on the
- * context stream without synchronising. */
+/* Same operator as ie_matvec_dev, for callers that must not allocate device memory during the call.
+ * (An extension of this library; the paper has no counterpart.) Who needs it: a host application that
+ * hands the library a fixed device-memory budget (its own pool owns the rest of the GPU, so a
+ * cudaMalloc inside the call could fail with out-of-memory at an arbitrary point), and latency-bound
+ * loops that cannot afford cudaMalloc/cudaFree, which may synchronise the whole device and stall the
+ * caller's other streams. The FFT intermediates go to one fixed 16 MiB device array that the library
+ * holds on every GPU that loads it, until the process exits: the x-transformed slab A
+ * (8 * 3 * nz * ny * Lx bytes), padded up to a 256-byte boundary, then the xy-transformed slab B
+ * (8 * 3 * nz * Ly * Lx bytes), with Lx/Ly the padded FFT lengths; a slab whose A and B do not fit is
+ * rejected with IE_EINVAL and nothing is enqueued. The Green spectra for the slab height must already
+ * exist (ie_create prepares the whole grid; other heights are prepared by one ie_matvec_dev or ie_solve
+ * call first), else IE_ESTATE. The passes use the default FFT tile shapes (the autotuner is not
+ * consulted, since timing candidates would need scratch of its own). The first call on each device
+ * looks up the array's device address on that device (the call runs on the context's device); make
+ * that first call before any stream capture. All calls share the array and it keeps the last call's
+ * contents: every element a call reads was written earlier in the same call, so nothing needs
+ * clearing, but calls that overlap on the GPU (different streams or contexts at the same time) race
+ * and give wrong results. x_dev, y_dev: distinct device arrays [3][nz][ny][nx] complex64; work is
+ * enqueued on the context stream without synchronising. */
 ie_status ie_matvec_dev_noalloc(ie_ctx* ctx, int32_t z0, int32_t nz, const void* x_dev, void* y_dev);
 
 /* Interaction field of eqs. 21/23: y = G^(ts) dsigma^(s) x for a source slab [zs0, zs0+nzs) and a
@@ -281,6 +288,13 @@ ie_status ie_profile_read(const ie_ctx* ctx, int32_t kclass, int64_t* launches, 
  * pencils per block). Writes at most len bytes including the terminating NUL; returns the length the
  * full text needs. */
 int32_t ie_tuned_tiles(char* buf, int32_t len);
+
+/* Testing hook (an extension of this library; the paper has no counterpart): after `after` more
+ * successful device allocations, the next one made by any context of this process reports
+ * out-of-memory without calling cudaMalloc, so callers can test their handling of IE_ENOMEM without
+ * exhausting a GPU. Fires once; a negative value switches it off. The call that meets the injected
+ * failure returns IE_ENOMEM and leaves its context usable (nothing half-allocated is kept). */
+void ie_debug_fail_allocation(int32_t after);
 
 /* Last error message of the context (never NULL; "" when none). */
 const char* ie_last_error(const ie_ctx* ctx);

@@ -39,6 +39,11 @@ static int next_pow2(int v) {
   return p;
 }
 
+// Host-side fault injection (ie_debug_fail_allocation): when this count reaches zero the next device
+// allocation reports out-of-memory without calling cudaMalloc, so the error paths can be tested without
+// exhausting a GPU. Negative: off.
+std::atomic<int> g_alloc_fail_countdown{-1};
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -51,6 +56,8 @@ struct DevBuf {
   cudaError_t ensure(size_t b) {
     if (b <= bytes && p) return cudaSuccess;
     release();
+    if (g_alloc_fail_countdown.load() >= 0 && g_alloc_fail_countdown.fetch_sub(1) == 0)
+      return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&p, b);
     if (e != cudaSuccess) {
       p = nullptr;
@@ -89,6 +96,7 @@ struct GmGraph {
 using namespace ie;
 
 struct ie_ctx {
+  int dev = 0;  // the CUDA device the context was created on (every call runs there)
   int nx = 0, ny = 0, nz = 0;
   long N = 0;
   double origin[3] = {0, 0, 0};
@@ -157,6 +165,35 @@ ie_status fail(ie_ctx* c, ie_status st, const std::string& msg) {
   if (c) c->err = msg;
   return st;
 }
+
+// Makes the context's device current for the duration of one library call and gives the calling
+// thread its own current device back afterwards, so a context works whichever device the caller has
+// selected (its buffers, streams and the no-allocation scratch all belong to that device).
+struct DevGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DevGuard(const ie_ctx* c) {
+    if (!c) return;
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      prev = -1;
+      ok = false;
+      return;
+    }
+    if (prev == c->dev) {
+      prev = -1;  // nothing to restore
+    } else if (cudaSetDevice(c->dev) != cudaSuccess) {
+      ok = false;
+    }
+  }
+  ~DevGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DevGuard(const DevGuard&) = delete;
+  DevGuard& operator=(const DevGuard&) = delete;
+};
+#define IE_ON_CTX_DEVICE(c)                                                          \
+  DevGuard ie_dev_guard_(c);                                                         \
+  if (!ie_dev_guard_.ok) return fail(const_cast<ie_ctx*>(c), IE_ECUDA, "cannot make the context's device current")
 
 #define CK(expr)                                                                              \
   do {                                                                                        \
@@ -1349,6 +1386,10 @@ ie_status ie_create(const ie_grid* grid, double h, double sigma0, double freq, i
     return IE_EINVAL;
   auto* c = new (std::nothrow) ie_ctx();
   if (!c) return IE_ENOMEM;
+  if (cudaGetDevice(&c->dev) != cudaSuccess) {
+    delete c;
+    return IE_ECUDA;
+  }
   c->nx = grid->nx;
   c->ny = grid->ny;
   c->nz = grid->nz;
@@ -1410,6 +1451,7 @@ ie_status ie_create(const ie_grid* grid, double h, double sigma0, double freq, i
 }
 
 ie_status ie_set_stream(ie_ctx* c, void* stream) {
+  IE_ON_CTX_DEVICE(c);
   if (!c) return IE_EINVAL;
   c->stream = reinterpret_cast<cudaStream_t>(stream);
   return IE_OK;
@@ -1444,6 +1486,7 @@ static ie_status set_contrast_dev_impl(ie_ctx* c, const double* s6_dev) {
 }
 
 ie_status ie_set_contrast(ie_ctx* c, const double* sigma6) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !sigma6) return fail(c, IE_EINVAL, "null argument");
   CK(c->s6_stage.ensure(sizeof(double) * 6 * c->N));
   CK(cudaMemcpyAsync(c->s6_stage.p, sigma6, sizeof(double) * 6 * c->N, cudaMemcpyHostToDevice, c->stream));
@@ -1451,12 +1494,14 @@ ie_status ie_set_contrast(ie_ctx* c, const double* sigma6) {
 }
 
 ie_status ie_set_contrast_dev(ie_ctx* c, const double* sigma6_dev) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !sigma6_dev) return fail(c, IE_EINVAL, "null argument");
   return set_contrast_dev_impl(c, sigma6_dev);
 }
 
 ie_status ie_solve(ie_ctx* c, int32_t n_src, const ie_dipole* src, int32_t n_rx, const double* rx, int32_t dd_mode,
                    double tol, const ie_opts* opts, double* H_out, ie_info* info) {
+  IE_ON_CTX_DEVICE(c);
   const auto t0 = std::chrono::steady_clock::now();
   if (!c) return IE_EINVAL;
   c->err.clear();
@@ -1563,7 +1608,8 @@ ie_status ie_solve_batch(int32_t n_items, ie_batch_item* items, int32_t max_conc
   for (size_t g = 0; g < ctxs.size(); ++g) {
     saved[g] = ctxs[g]->stream;
     if (!saved[g]) {
-      if (cudaStreamCreateWithFlags(&owned[g], cudaStreamNonBlocking) != cudaSuccess) {
+      DevGuard on_dev(ctxs[g]);
+      if (!on_dev.ok || cudaStreamCreateWithFlags(&owned[g], cudaStreamNonBlocking) != cudaSuccess) {
         for (size_t h = 0; h < g; ++h)
           if (owned[h]) cudaStreamDestroy(owned[h]);
         return IE_ECUDA;
@@ -1593,6 +1639,7 @@ ie_status ie_solve_batch(int32_t n_items, ie_batch_item* items, int32_t max_conc
   for (auto& t : pool) t.join();
   for (size_t g = 0; g < ctxs.size(); ++g) {
     if (owned[g]) {
+      DevGuard on_dev(ctxs[g]);
       cudaStreamSynchronize(owned[g]);
       cudaStreamDestroy(owned[g]);
       ctxs[g]->stream = saved[g];
@@ -1604,6 +1651,7 @@ ie_status ie_solve_batch(int32_t n_items, ie_batch_item* items, int32_t max_conc
 }
 
 ie_status ie_set_initial_field_dev(ie_ctx* c, const double* E_dev) {
+  IE_ON_CTX_DEVICE(c);
   if (!c) return IE_EINVAL;
   if (!E_dev) {
     c->has_init = false;
@@ -1616,6 +1664,7 @@ ie_status ie_set_initial_field_dev(ie_ctx* c, const double* E_dev) {
 }
 
 ie_status ie_get_field_dev(ie_ctx* c, double* E_dev) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !E_dev) return fail(c, IE_EINVAL, "null argument");
   if (!c->has_field) return fail(c, IE_ESTATE, "no solve has run");
   CK(cudaMemcpyAsync(E_dev, c->E.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToDevice, c->stream));
@@ -1623,6 +1672,7 @@ ie_status ie_get_field_dev(ie_ctx* c, double* E_dev) {
 }
 
 ie_status ie_incident_field_dev(ie_ctx* c, const ie_dipole* src, double* E0_dev) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !src || !E0_dev) return fail(c, IE_EINVAL, "null argument");
   CKS(check_point(c, src->pos));
   KL(IE_K_FIELD, 48.0 * c->N,
@@ -1632,6 +1682,7 @@ ie_status ie_incident_field_dev(ie_ctx* c, const ie_dipole* src, double* E0_dev)
 }
 
 ie_status ie_get_field(ie_ctx* c, double* E_out) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !E_out) return fail(c, IE_EINVAL, "null argument");
   if (!c->has_field) return fail(c, IE_ESTATE, "no solve has run");
   CK(cudaMemcpyAsync(E_out, c->E.p, sizeof(double2) * 3 * c->N, cudaMemcpyDeviceToHost, c->stream));
@@ -1640,6 +1691,7 @@ ie_status ie_get_field(ie_ctx* c, double* E_out) {
 }
 
 ie_status ie_matvec(ie_ctx* c, int32_t precision, int32_t z0, int32_t nz, const double* x, double* y) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !x || !y) return fail(c, IE_EINVAL, "null argument");
   const long nb = (long)nz * c->ny * c->nx;
   DevBuf xd, yd, xs, ys;
@@ -1673,6 +1725,7 @@ ie_status ie_matvec(ie_ctx* c, int32_t precision, int32_t z0, int32_t nz, const 
 }
 
 ie_status ie_matvec_contraction(ie_ctx* c, int32_t precision, int32_t z0, int32_t nz, const double* x, double* y) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !x || !y) return fail(c, IE_EINVAL, "null argument");
   if (precision != IE_PREC_MIXED && precision != IE_PREC_FP64) return fail(c, IE_EINVAL, "bad precision");
   const long nb = (long)nz * c->ny * c->nx;
@@ -1700,6 +1753,7 @@ ie_status ie_matvec_contraction(ie_ctx* c, int32_t precision, int32_t z0, int32_
 }
 
 ie_status ie_matvec_dev(ie_ctx* c, int32_t z0, int32_t nz, const void* x_dev, void* y_dev) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !x_dev || !y_dev || x_dev == y_dev) return fail(c, IE_EINVAL, "bad argument");
   BlockOp<float> A;
   CKS(make_block<float>(c, z0, nz, &A));
@@ -1707,6 +1761,7 @@ ie_status ie_matvec_dev(ie_ctx* c, int32_t z0, int32_t nz, const void* x_dev, vo
 }
 
 ie_status ie_interaction(ie_ctx* c, int32_t zs0, int32_t nzs, int32_t zt0, int32_t nzt, const double* x, double* y) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !x || !y) return fail(c, IE_EINVAL, "null argument");
   if (zs0 < 0 || nzs < 1 || zs0 + nzs > c->nz || zt0 < 0 || nzt < 1 || zt0 + nzt > c->nz)
     return fail(c, IE_EINVAL, "slab outside the grid");
@@ -1726,12 +1781,14 @@ ie_status ie_interaction(ie_ctx* c, int32_t zs0, int32_t nzs, int32_t zt0, int32
 
 ie_status ie_gmres(ie_ctx* c, int32_t precision, int32_t z0, int32_t nz, const double* b, const double* x0, double tol,
                    int32_t restart, int32_t max_iter, double* x, int32_t* iters, double* rel) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !b || !x || !(tol > 0) || max_iter < 0) return fail(c, IE_EINVAL, "bad argument");
   return precision == IE_PREC_FP64 ? gmres_host<double>(c, z0, nz, b, x0, tol, restart, max_iter, x, iters, rel)
                                    : gmres_host<float>(c, z0, nz, b, x0, tol, restart, max_iter, x, iters, rel);
 }
 
 ie_status ie_green_spectrum(ie_ctx* c, int32_t nz_set, int32_t comp, double* out, int32_t* dims) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !out || comp < 0 || comp > 5 || nz_set < 1 || nz_set > c->nz) return fail(c, IE_EINVAL, "bad argument");
   SpecSet* S = nullptr;
   CKS(get_spec(c, nz_set, &S));
@@ -1747,6 +1804,7 @@ ie_status ie_green_spectrum(ie_ctx* c, int32_t nz_set, int32_t comp, double* out
 }
 
 ie_status ie_incident_field(ie_ctx* c, const ie_dipole* src, double* E0_out) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !src || !E0_out) return fail(c, IE_EINVAL, "null argument");
   CKS(check_point(c, src->pos));
   DevBuf e;
@@ -1761,6 +1819,7 @@ ie_status ie_incident_field(ie_ctx* c, const ie_dipole* src, double* E0_out) {
 
 ie_status ie_receiver_fields(ie_ctx* c, const double* E, const ie_dipole* src, int32_t n_rx, const double* rx,
                              double* H_out) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !E || !src || (n_rx > 0 && (!rx || !H_out)) || n_rx < 0) return fail(c, IE_EINVAL, "bad argument");
   if (!c->has_contrast) return fail(c, IE_ESTATE, "no contrast set");
   for (int r = 0; r < n_rx; ++r) CKS(check_point(c, rx + 3 * r));
@@ -1792,6 +1851,7 @@ ie_status ie_fft_dims(const ie_ctx* c, int32_t nz_set, int32_t* dims) {
 }
 
 ie_status ie_profile_enable(ie_ctx* c, int32_t on) {
+  IE_ON_CTX_DEVICE(c);
   if (!c) return IE_EINVAL;
   CK(sync(c));
   auto& P = c->prof;
@@ -1834,10 +1894,13 @@ int32_t ie_tuned_tiles(char* buf, int32_t len) {
   return (int32_t)txt.size() + 1;
 }
 
+void ie_debug_fail_allocation(int32_t after) { g_alloc_fail_countdown.store(after < 0 ? -1 : after); }
+
 const char* ie_last_error(const ie_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 void ie_destroy(ie_ctx* c) {
   if (!c) return;
+  DevGuard on_dev(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   delete c;
 }
@@ -1856,12 +1919,15 @@ constexpr int kMaxDevices = 64;
 void* g_noalloc_ptr[kMaxDevices] = {};
 std::mutex g_noalloc_mu;
 
-// Device address of the scratch array on the current device, looked up once per device.
-cudaError_t noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of the scratch array on device `dev`, looked up once per device. The caller has made
+// `dev` current (every entry point runs on its context's device), which is what the lookup needs: the
+// array's host-side name is only a stand-in, and each device holds its own copy.
+cudaError_t noalloc_scratch(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return e;
+  if (cur != dev) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
@@ -1875,6 +1941,7 @@ cudaError_t noalloc_scratch(void** out) {
 }  // namespace
 
 extern "C" ie_status ie_matvec_dev_noalloc(ie_ctx* c, int32_t z0, int32_t nz, const void* x_dev, void* y_dev) {
+  IE_ON_CTX_DEVICE(c);
   if (!c || !x_dev || !y_dev || x_dev == y_dev) return fail(c, IE_EINVAL, "bad argument");
   if (z0 < 0 || nz < 1 || z0 + nz > c->nz) return fail(c, IE_EINVAL, "slab outside the grid");
   if (!c->has_contrast) return fail(c, IE_ESTATE, "no contrast set");
@@ -1893,7 +1960,7 @@ extern "C" ie_status ie_matvec_dev_noalloc(ie_ctx* c, int32_t z0, int32_t nz, co
                 "slab needs " + std::to_string(need) + " bytes of scratch, above the " +
                     std::to_string(kNoAllocScratchBytes) + "-byte limit of the no-allocation operator");
   void* base = nullptr;
-  CK(noalloc_scratch(&base));
+  CK(noalloc_scratch(c->dev, &base));
   float2* A = reinterpret_cast<float2*>(base);
   float2* B = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(base) + b_off);
   const float2* x = reinterpret_cast<const float2*>(x_dev);

@@ -96,6 +96,7 @@ _SIGS = {
     "ie_profile_read": (ct.c_int, [_P, ct.c_int32, ct.POINTER(ct.c_int64), _D, _D]),
     "ie_tuned_tiles": (ct.c_int32, [ct.c_char_p, ct.c_int32]),
     "ie_last_error": (ct.c_char_p, [_P]),
+    "ie_debug_fail_allocation": (None, [ct.c_int32]),
     "ie_destroy": (None, [_P]),
     # include/ie_fno.h
     "ie_fno_create": (ct.c_int, [ct.c_int32] * 9 + [ct.POINTER(_P)]),
@@ -254,7 +255,8 @@ class Context:
         self._check(_lib.ie_matvec_dev(self.ptr, int(z0), int(nz), _P(_addr(x_dev)), _P(_addr(y_dev))))
 
     def matvec_dev_noalloc(self, x_dev, y_dev, z0=0, nz=None):
-        """ie_matvec_dev without any device allocation (fixed 16 MiB library scratch; see ie.h)."""
+        """ie_matvec_dev without any device allocation, for callers with a fixed device-memory budget:
+        the FFT intermediates use a fixed 16 MiB library-owned array per GPU (see ie.h)."""
         nz = self.nz if nz is None else nz
         self._check(_lib.ie_matvec_dev_noalloc(self.ptr, int(z0), int(nz), _P(_addr(x_dev)), _P(_addr(y_dev))))
 
@@ -447,6 +449,12 @@ def fno_flat(params) -> np.ndarray:
             a = np.stack([a.real, a.imag], axis=-1)
         parts.append(a.astype(np.float32).ravel())
     return np.concatenate(parts)
+
+
+def debug_fail_allocation(after: int):
+    """ie_debug_fail_allocation: make the device allocation after `after` more successful ones report
+    out-of-memory (testing hook; negative switches it off)."""
+    _lib.ie_debug_fail_allocation(int(after))
 
 
 def tuned_tiles() -> str:
