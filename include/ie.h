@@ -284,8 +284,9 @@ ie_status ie_profile_enable(ie_ctx* ctx, int32_t on);
 ie_status ie_profile_read(const ie_ctx* ctx, int32_t kclass, int64_t* launches, double* ms, double* algo_bytes);
 
 /* Tile shapes chosen so far by the FFT-tile autotuner of this process, as text (one line per pass
- * shape: pass, element bytes, pencil length, Lx, Ly, slab heights, chosen variant; variant 1 = half the
- * pencils per block). Writes at most len bytes including the terminating NUL; returns the length the
+ * shape: pass, element bytes, pencil length, Lx, Ly, slab heights, chosen variant, then the measured
+ * microseconds per launch of every variant; variant 1 = half the pencils per block, z-pass variants 2/3
+ * stage their input with TMA, 4 keeps whole pencils inside one warp). Writes at most len bytes including the terminating NUL; returns the length the
  * full text needs. */
 int32_t ie_tuned_tiles(char* buf, int32_t len);
 

@@ -4,6 +4,7 @@
 #pragma once
 #include "conv.cuh"
 #include "conv_kernels.cuh"
+#include "conv_p3w.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -186,6 +187,22 @@ static cudaError_t p3_launch(const C<T>* Bin, long in_cs, int nzs, int os, C<T>*
   return cudaGetLastError();
 }
 
+// Variant 4: warp-resident pencils with the spectra in registers (k_p3_warp), complex64 and L <= 512.
+template <typename T, int N>
+static cudaError_t p3_warp_launch(const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt,
+                                  int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value && N <= 512) {
+    using Cfg = P3WCfg<N>;
+    if (in_cs > INT32_MAX || out_cs > INT32_MAX || 3L * in_cs > INT32_MAX || 3L * out_cs > INT32_MAX)
+      return cudaErrorInvalidValue;
+    dim3 blk(32 * Cfg::NW), grd((unsigned)((Lx + Cfg::LANES - 1) / Cfg::LANES), (unsigned)Ly);
+    k_p3_warp<N><<<grd, blk, 0, s>>>(Bin, (int)in_cs, nzs, os, Bout, (int)out_cs, nzt, ot, G, Lx, Ly, tw);
+    return cudaGetLastError();
+  } else {
+    return p3_launch<T, N, 1, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, nullptr, s);
+  }
+}
+
 template <typename T>
 cudaError_t ConvLaunch<T>::p3(int L, int variant, const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout,
                               long out_cs, int nzt, int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err,
@@ -197,6 +214,7 @@ cudaError_t ConvLaunch<T>::p3(int L, int variant, const C<T>* Bin, long in_cs, i
       case 1: return p3_launch<T, N, 2, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
       case 2: return p3_launch<T, N, 1, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
       case 3: return p3_launch<T, N, 2, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
+      case 4: return p3_warp_launch<T, N>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, s);          \
       default: return p3_launch<T, N, 1, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
     }
     IE_FOR_EACH_L(IE_CASE)

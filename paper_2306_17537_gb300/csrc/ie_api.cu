@@ -357,7 +357,8 @@ template <typename T> ie_status ensure_conv_ws(ie_ctx* c, int zcap) {
 // block; P3 has each also with TMA staging of its input pencils (four variants). The first convolution
 // of a new shape times every variant on the live buffers
 // (three timed launches each after a warm-up; the work is data independent) and keeps the fastest for
-// the rest of the process. Variants produce bit-identical results.
+// the rest of the process. Variants 0-3 produce bit-identical results; the warp-resident z pass
+// (variant 4, complex64) sums the Green product in another order (differences at rounding level).
 struct TuneKey {
   int kind, bytes, L, Lx, Ly, nz, nz2;
   bool operator<(const TuneKey& o) const {
@@ -365,6 +366,7 @@ struct TuneKey {
   }
 };
 std::map<TuneKey, int> g_tuned;
+std::map<TuneKey, std::vector<float>> g_tune_ms;  // mean time of one launch of each variant (ms)
 std::mutex g_tune_mu;
 
 int tuned_variant(const TuneKey& k) {
@@ -380,6 +382,7 @@ template <class F> cudaError_t tune(ie_ctx* c, const TuneKey& k, F&& run, int* b
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   float best_ms = 1e30f;
   *best = 0;
+  std::vector<float> times;
   for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
     e = run(v);  // warm-up (module load, caches)
     if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
@@ -388,6 +391,7 @@ template <class F> cudaError_t tune(ie_ctx* c, const TuneKey& k, F&& run, int* b
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    times.push_back(ms / 3.f);
     if (e == cudaSuccess && ms < best_ms) {
       best_ms = ms;
       *best = v;
@@ -398,6 +402,7 @@ template <class F> cudaError_t tune(ie_ctx* c, const TuneKey& k, F&& run, int* b
   if (e == cudaSuccess) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tuned[k] = *best;
+    g_tune_ms[k] = times;
   }
   return e;
 }
@@ -457,7 +462,7 @@ ie_status conv(ie_ctx* c, const SpecSet* S, const FieldC<T>* x, long x_cs, int z
   if (v2 < 0) CK(tune(c, k2, p2, &v2));
   KL(k0 + 1, 3 * sz * nzs * c->Lx * (double)(c->ny + c->Ly), p2(v2));
   if (v3 < 0) {  // P3 works in place: tune on the live B, then rebuild B from x before the real pass
-    CK(tune(c, k3, p3, &v3, kP3TileVariants));
+    CK(tune(c, k3, p3, &v3, std::is_same<T, float>::value ? kP3TileVariants : 4));
     CK(p1());
     CK(p2(v2));
   }
@@ -1883,7 +1888,12 @@ int32_t ie_tuned_tiles(char* buf, int32_t len) {
       const TuneKey& k = kv.first;
       txt += std::string(pass[k.kind]) + " bytes=" + std::to_string(k.bytes) + " L=" + std::to_string(k.L) +
              " Lx=" + std::to_string(k.Lx) + " Ly=" + std::to_string(k.Ly) + " nz=" + std::to_string(k.nz) + "/" +
-             std::to_string(k.nz2) + " variant=" + std::to_string(kv.second) + "\n";
+             std::to_string(k.nz2) + " variant=" + std::to_string(kv.second) + " us=";
+      const auto it = g_tune_ms.find(k);
+      if (it != g_tune_ms.end())
+        for (size_t v = 0; v < it->second.size(); ++v)
+          txt += (v ? "/" : "") + std::to_string((int)std::lround(1000.0 * it->second[v]));
+      txt += "\n";
     }
   }
   if (buf && len > 0) {
