@@ -90,6 +90,12 @@ typedef struct {
                              fixed-point sweeps of Algorithm 1 (the paper's conclusion); 0 (default) */
   int32_t outer_restart;  /* restart length of that outer iteration (default 10, at most 127) */
   double outer_inner_tol; /* block tolerance inside its preconditioner sweeps (default 0.1) */
+  int32_t concurrent_blocks; /* 1 with IE_DD_JACOBI: the sub-domain solves of a sweep run at the same time,
+                                each on its own stream and workspace (eq. 23 makes them independent; the
+                                closing remark of Section 2.3 calls them parallelisable); their right-hand
+                                sides and results are exchanged with the whole-grid field on the context
+                                stream. Costs one Krylov basis per sub-domain. 0 (default): one after
+                                another. Ignored for the other modes. */
 } ie_opts;
 
 #define IE_MAX_HISTORY 128

@@ -121,6 +121,14 @@ struct ie_ctx {
   Tape* tape = nullptr;  // non-null while a graph is being captured
   bool has_contrast = false;
   std::vector<SpecSet*> specs;
+  // Concurrent block-Jacobi solves (ie_opts.concurrent_blocks): one worker context per sub-domain, holding
+  // that slab's contrast, its own stream and Krylov/FFT workspaces, and the parent's spectra for the
+  // slab height (borrowed, not owned). Built for a split and reused while the split stays the same.
+  std::vector<ie_ctx*> workers;
+  std::vector<int> worker_split;
+  long contrast_version = 0, worker_contrast_version = -1;
+  std::vector<SpecSet*> borrowed;  // spectra owned by the parent context (workers only)
+  bool owns_stream = false;        // workers create their own non-blocking stream
 
   DevBuf A32, B32, A64, B64;  // convolution workspaces
   long zcap32 = 0, zcap64 = 0;
@@ -149,6 +157,11 @@ struct ie_ctx {
   } prof;
 
   ~ie_ctx() {
+    for (auto* w : workers) delete w;
+    if (owns_stream && stream) {
+      cudaStreamSynchronize(stream);
+      cudaStreamDestroy(stream);
+    }
     for (auto* g : gm_graphs) delete g;
     for (auto st : cap)
       if (st) cudaStreamDestroy(st);
@@ -278,6 +291,11 @@ template <> const dfc* spec<df>(const SpecSet* s) { return s->Gdf.as<dfc>(); }
 
 // Green spectra for a slab of nz_set cells: FP64 tabulation -> FP64 3D FFT -> scaled octants.
 ie_status get_spec(ie_ctx* c, int nz_set, SpecSet** out) {
+  for (auto* s : c->borrowed)
+    if (s->nz_set == nz_set) {
+      *out = s;
+      return IE_OK;
+    }
   for (auto* s : c->specs)
     if (s->nz_set == nz_set) {
       *out = s;
@@ -533,6 +551,126 @@ template <typename T> ie_status make_block(ie_ctx* c, int z0, int nz, BlockOp<T>
   if (contract) CKS(ensure_contract(c));
   *op = BlockOp<T>{c, z0, nz, S, contract};
   return IE_OK;
+}
+
+// Worker context for the slab [z0, z0 + nz) of c (concurrent block-Jacobi solves): the same cell size,
+// background and frequency on a grid of nz planes, its own non-blocking stream, error flag and
+// workspaces, and the parent's spectra for the slab height. Its twiddles and contrast are copied from
+// the parent on the parent's stream (prepare_workers orders the worker streams after those copies).
+ie_status make_worker(ie_ctx* c, int z0, int nz, ie_ctx** out) {
+  *out = nullptr;
+  SpecSet* S = nullptr;
+  CKS(get_spec(c, nz, &S));
+  auto* w = new (std::nothrow) ie_ctx();
+  if (!w) return fail(c, IE_ENOMEM, "allocating a worker context");
+  w->dev = c->dev;
+  w->nx = c->nx;
+  w->ny = c->ny;
+  w->nz = nz;
+  w->N = (long)nz * c->nx * c->ny;
+  for (int a = 0; a < 3; ++a) w->origin[a] = c->origin[a];
+  w->origin[2] += z0 * c->h;
+  w->h = c->h;
+  w->sigma0 = c->sigma0;
+  w->freq = c->freq;
+  w->omega = c->omega;
+  w->k0 = c->k0;
+  w->self = c->self;
+  w->Lx = c->Lx;
+  w->Ly = c->Ly;
+  w->borrowed.push_back(S);
+  auto bad = [&](ie_status st, const std::string& what) {
+    delete w;
+    return fail(c, st, what);
+  };
+  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bad(IE_ECUDA, "creating a worker stream");
+  w->owns_stream = true;
+  if (cudaHostAlloc(reinterpret_cast<void**>(&w->kerr), sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+    w->kerr = nullptr;
+    return bad(IE_ENOMEM, "allocating a worker flag");
+  }
+  *w->kerr = 0;
+  cudaError_t e = w->tw64.ensure(sizeof(double2) * TWN);
+  if (e == cudaSuccess) e = w->tw32.ensure(sizeof(float2) * TWN);
+  if (e == cudaSuccess) e = w->twdf.ensure(sizeof(dfc) * TWN);
+  if (e == cudaSuccess) e = w->ds64.ensure(sizeof(double) * 6 * w->N);
+  if (e == cudaSuccess) e = w->ds32.ensure(sizeof(float) * 6 * w->N);
+  if (e != cudaSuccess) return bad(e == cudaErrorMemoryAllocation ? IE_ENOMEM : IE_ECUDA, "worker buffers");
+  e = cudaMemcpyAsync(w->tw64.p, c->tw64.p, sizeof(double2) * TWN, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w->tw32.p, c->tw32.p, sizeof(float2) * TWN, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w->twdf.p, c->twdf.p, sizeof(dfc) * TWN, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return bad(IE_ECUDA, "copying twiddles to a worker");
+  *out = w;
+  return IE_OK;
+}
+
+// Worker contexts for the sub-domains of `split`, with the current contrast (copied on the parent
+// stream; see order_workers).
+ie_status prepare_workers(ie_ctx* c, const std::vector<int>& split) {
+  const int M = (int)split.size() - 1;
+  const long nxy = (long)c->nx * c->ny;
+  if (c->worker_split != split) {
+    for (auto* w : c->workers) delete w;
+    c->workers.clear();
+    c->worker_split.clear();
+    std::vector<ie_ctx*> ws;
+    for (int i = 0; i < M; ++i) {
+      ie_ctx* w = nullptr;
+      const ie_status st = make_worker(c, split[i], split[i + 1] - split[i], &w);
+      if (st != IE_OK) {
+        for (auto* x : ws) delete x;
+        return st;
+      }
+      ws.push_back(w);
+    }
+    c->workers = ws;
+    c->worker_split = split;
+    c->worker_contrast_version = -1;
+  }
+  if (c->worker_contrast_version != c->contrast_version) {
+    for (int i = 0; i < M; ++i) {
+      ie_ctx* w = c->workers[i];
+      const long nb = w->N, off = (long)split[i] * nxy;
+      for (int k = 0; k < 6; ++k) {
+        CK(cudaMemcpyAsync(w->ds64.as<double>() + k * nb, c->ds64.as<double>() + k * c->N + off, sizeof(double) * nb,
+                           cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(w->ds32.as<float>() + k * nb, c->ds32.as<float>() + k * c->N + off, sizeof(float) * nb,
+                           cudaMemcpyDeviceToDevice, c->stream));
+      }
+      w->has_contrast = true;
+      w->contract_ready = false;
+    }
+    c->worker_contrast_version = c->contrast_version;
+  }
+  for (auto* w : c->workers) {
+    if (w->prof.on != c->prof.on) {
+      w->prof.on = c->prof.on;
+      w->prof.used = 0;
+    }
+  }
+  return IE_OK;
+}
+
+// Orders the work enqueued next on every worker stream after everything enqueued so far on the parent
+// stream.
+ie_status order_workers(ie_ctx* c, cudaEvent_t ev) {
+  CK(cudaEventRecord(ev, c->stream));
+  for (auto* w : c->workers) CK(cudaStreamWaitEvent(w->stream, ev, 0));
+  return IE_OK;
+}
+
+// Adds a worker's launch accounting to its parent's and clears it (after the worker stream drained).
+void fold_profile(ie_ctx* c, ie_ctx* w) {
+  for (int k = 0; k < IE_K_COUNT; ++k) {
+    c->prof.launches[k] += w->prof.launches[k];
+    c->prof.ms[k] += w->prof.ms[k];
+    c->prof.bytes[k] += w->prof.bytes[k];
+    w->prof.launches[k] = 0;
+    w->prof.ms[k] = 0.0;
+    w->prof.bytes[k] = 0.0;
+  }
 }
 
 ie_status ensure_scalars(ie_ctx* c) {
@@ -1015,7 +1153,7 @@ struct SolveCfg {
   int dd_mode;
   std::vector<int> split;
   int restart, max_outer, max_inner, precision, adaptive, contraction, graph;
-  int outer_krylov, outer_restart;
+  int outer_krylov, outer_restart, concurrent;
   double fixed_tol, tol, outer_inner_tol;
 };
 
@@ -1294,13 +1432,115 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
     }
     return IE_OK;
   };
+  // The same sweep for block Jacobi with the sub-domain solves in flight together (concurrent_blocks):
+  // norms, tolerances and right-hand sides are formed on the context stream as above, then every block
+  // is solved by its worker context (own stream, own Krylov basis) on its own host thread, and the
+  // corrections are added to the whole-grid field on the context stream. Eq. 23: in a Jacobi sweep the
+  // block solves read only the previous sweep's field, so they are independent.
+  const bool conc = cfg.concurrent && cfg.dd_mode == IE_DD_JACOBI && M > 1;
+  if (conc) CKS(prepare_workers(c, cfg.split));
+  auto sweep_conc = [&](double2* Rb, double2* Eb, double precond_tol, int* sweep_its) -> ie_status {
+    const bool pre = precond_tol > 0;
+    struct Job {
+      int i = 0;
+      double tol = 0.0;
+      GmresOut go;
+      ie_status st = IE_OK;
+    };
+    std::vector<Job> jobs;
+    for (int i = 0; i < M; ++i) {
+      if (!blk_active[i]) continue;
+      const BlockOp<T>& A = ops[i];
+      const long nb = A.nb(), off = (long)A.z0 * nxy;
+      double2* Ri = Rb + off;
+      double2* Ei = Eb + off;
+      double rnorm;
+      CKS(norm_c128(c, Ri, c->N, nullptr, 0, nb, &rnorm));
+      if (rnorm == 0.0) continue;
+      double bnorm = rnorm;  // |b_i| = |R_i + A_ii E_i| (eq. 23)
+      if (pre) {
+      } else if (keep_ae) {
+        CKS(norm_c128(c, Ri, c->N, c->AEb.as<float2>() + ae_off[i], nb, nb, &bnorm));
+      } else if (std::is_same<T, float>::value) {
+        KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(Ei, c->N, reinterpret_cast<float2*>(dx), nb, nb, s));
+        CKS(A.apply_conv(dx, t2));
+        CKS(norm_c128(c, Ri, c->N, reinterpret_cast<const float2*>(t2), nb, nb, &bnorm));
+      } else {
+        KL(IE_K_FIELD, 96.0 * nb, launch_copy_c128(Ei, c->N, reinterpret_cast<double2*>(dx), nb, nb, s));
+        CKS(A.apply_conv(dx, t2));
+        KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(Ri, c->N, reinterpret_cast<double2*>(t2), nb, nb, s));
+        CKS(norm_c128(c, reinterpret_cast<const double2*>(t2), nb, nullptr, 0, nb, &bnorm));
+      }
+      double tol_i = pre ? precond_tol : (cfg.adaptive ? e / 10.0 : cfg.fixed_tol) * bnorm / rnorm;
+      if (std::is_same<T, float>::value) tol_i = std::max(tol_i, 1e-6);
+      tol_i = std::min(tol_i, 0.5);
+      ie_ctx* w = c->workers[i];
+      CK(w->kb.ensure(sizeof(C<T>) * 3 * nb));
+      CK(w->kx.ensure(sizeof(C<T>) * 3 * nb));
+      if (std::is_same<T, float>::value)
+        KL(IE_K_FIELD, 72.0 * nb, launch_c128_to_c64(Ri, c->N, w->kb.as<float2>(), nb, nb, s));
+      else
+        KL(IE_K_FIELD, 96.0 * nb, launch_copy_c128(Ri, c->N, w->kb.as<double2>(), nb, nb, s));
+      Job j;
+      j.i = i;
+      j.tol = tol_i;
+      jobs.push_back(j);
+    }
+    if (jobs.empty()) return IE_OK;
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    const ie_status ost = order_workers(c, ev);
+    cudaEventDestroy(ev);  // released once the recorded work completes
+    CKS(ost);
+    std::vector<std::thread> pool;
+    for (auto& job : jobs)
+      pool.emplace_back([&, jp = &job]() {
+        cudaSetDevice(c->dev);
+        ie_ctx* w = c->workers[jp->i];
+        BlockOp<T> A;
+        jp->st = make_block<T>(w, 0, w->nz, &A, cfg.contraction != 0);
+        C<T>* rhs_w = w->kb.template as<C<T>>();
+        C<T>* dx_w = w->kx.template as<C<T>>();
+        if (jp->st == IE_OK)
+          jp->st = cfg.graph ? gmres_graph<T>(w, A, rhs_w, dx_w, jp->tol, cfg.restart, cfg.max_inner, &jp->go)
+                             : gmres<T>(w, A, rhs_w, dx_w, true, jp->tol, cfg.restart, cfg.max_inner, &jp->go);
+        if (jp->st == IE_OK) jp->st = A.to_field(dx_w);
+        if (jp->st == IE_OK && sync(w) != cudaSuccess) jp->st = fail(w, IE_ECUDA, "sub-domain solve on its stream");
+      });
+    for (auto& t : pool) t.join();
+    for (const auto& job : jobs)
+      if (job.st != IE_OK) return fail(c, job.st, "sub-domain " + std::to_string(job.i) + ": " + c->workers[job.i]->err);
+    for (const auto& job : jobs) {  // every worker stream has drained: add the corrections
+      ie_ctx* w = c->workers[job.i];
+      fold_profile(c, w);
+      const long nb = ops[job.i].nb(), off = (long)ops[job.i].z0 * nxy;
+      double2* Ei = Eb + off;
+      if (keep_ae && !pre && job.go.iters > 0)  // A_ii delta = rhs - r (r: the final true residual)
+        KL(IE_K_FIELD, 96.0 * nb,
+           launch_add_diff_c64(c->AEb.as<float2>() + ae_off[job.i], w->kb.as<float2>(), w->kt1.as<float2>(), 3 * nb,
+                               s));
+      if (std::is_same<T, float>::value)
+        KL(IE_K_FIELD, 120.0 * nb, launch_add_c64_to_c128(w->kx.as<float2>(), nb, Ei, c->N, nb, s));
+      else
+        KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(w->kx.as<double2>(), nb, Ei, c->N, nb, s));
+      inner_ok = inner_ok && job.go.converged;
+      *sweep_its += job.go.iters;
+      info->gmres_iters_total += job.go.iters;
+      info->reorth_passes += job.go.reorth;
+      info->matvecs += job.go.matvecs;
+    }
+    return IE_OK;
+  };
+  auto sweep_any = [&](double2* Rb, double2* Eb, double precond_tol, int* sweep_its) -> ie_status {
+    return conc ? sweep_conc(Rb, Eb, precond_tol, sweep_its) : sweep(Rb, Eb, precond_tol, sweep_its);
+  };
   int sweeps = 0;
   if (cfg.outer_krylov && cfg.dd_mode != IE_DD_NONE) {
-    CKS(fgmres_outer<T>(c, cfg, blk_active, sweep, e0norm, &e, &sweeps, info, record, fast_ok));
+    CKS(fgmres_outer<T>(c, cfg, blk_active, sweep_any, e0norm, &e, &sweeps, info, record, fast_ok));
   } else {
     while (e > cfg.tol && sweeps < cfg.max_outer) {
       int sweep_its = 0;
-      CKS(sweep(c->R.as<double2>(), c->E.as<double2>(), 0.0, &sweep_its));
+      CKS(sweep_any(c->R.as<double2>(), c->E.as<double2>(), 0.0, &sweep_its));
       sweeps++;
       CKS(full_residual(c, e0norm, &e, fast_ok && e > kFastResidualAbove));
       if (record && info->n_history < IE_MAX_HISTORY) {
@@ -1487,6 +1727,7 @@ static ie_status set_contrast_dev_impl(ie_ctx* c, const double* s6_dev) {
   c->has_contrast = true;
   c->has_field = false;
   c->contract_ready = false;
+  c->contrast_version++;
   return IE_OK;
 }
 
@@ -1532,6 +1773,8 @@ ie_status ie_solve(ie_ctx* c, int32_t n_src, const ie_dipole* src, int32_t n_rx,
   cfg.outer_krylov = o.outer_krylov;
   cfg.outer_restart = o.outer_restart > 0 ? o.outer_restart : 10;
   cfg.outer_inner_tol = o.outer_inner_tol > 0 ? o.outer_inner_tol : 0.1;
+  cfg.concurrent = o.concurrent_blocks;
+  if (o.concurrent_blocks != 0 && o.concurrent_blocks != 1) return fail(c, IE_EINVAL, "concurrent_blocks must be 0 or 1");
   if (o.outer_krylov != 0 && o.outer_krylov != 1) return fail(c, IE_EINVAL, "outer_krylov must be 0 or 1");
   if (o.graph != 0 && o.graph != 1) return fail(c, IE_EINVAL, "graph must be 0 or 1");
   if (o.contraction != 0 && o.contraction != 1) return fail(c, IE_EINVAL, "contraction must be 0 or 1");

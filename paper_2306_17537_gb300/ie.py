@@ -39,7 +39,7 @@ class ie_opts(ct.Structure):
                 ("max_outer", ct.c_int32), ("max_inner", ct.c_int32), ("precision", ct.c_int32),
                 ("adaptive", ct.c_int32), ("fixed_tol", ct.c_double), ("contraction", ct.c_int32),
                 ("graph", ct.c_int32), ("outer_krylov", ct.c_int32), ("outer_restart", ct.c_int32),
-                ("outer_inner_tol", ct.c_double)]
+                ("outer_inner_tol", ct.c_double), ("concurrent_blocks", ct.c_int32)]
 
 
 class ie_batch_item(ct.Structure):
@@ -467,7 +467,7 @@ def tuned_tiles() -> str:
 
 def make_opts(n_blocks=1, z_split=None, restart=30, max_outer=50, max_inner=600, precision=IE_PREC_MIXED,
               adaptive=True, fixed_tol=1e-6, contraction=False, graph=False, outer_krylov=False, outer_restart=10,
-              outer_inner_tol=0.1) -> ie_opts:
+              outer_inner_tol=0.1, concurrent_blocks=False) -> ie_opts:
     o = ie_default_opts()
     o.n_blocks = int(n_blocks)
     if z_split is not None:
@@ -480,6 +480,7 @@ def make_opts(n_blocks=1, z_split=None, restart=30, max_outer=50, max_inner=600,
     o.contraction = int(bool(contraction))
     o.graph = int(bool(graph))
     o.outer_krylov, o.outer_restart, o.outer_inner_tol = int(bool(outer_krylov)), int(outer_restart), float(outer_inner_tol)
+    o.concurrent_blocks = int(bool(concurrent_blocks))
     return o
 
 

@@ -207,6 +207,84 @@ def config2(seed: int = 0, scale: int = 1) -> Workload:
                     z_split=[0, nz // 2, nz], tol=1e-6, restart=40)
 
 
+def faulted_ti_with_ellipsoids(grid: Grid, seed: int, n_layers: int = 7, ratio_max: float = 10.0,
+                               dip_max_deg: float = 30.0, n_ellipsoids: int = 5) -> np.ndarray:
+    """Dipping TI layers offset by a planar fault, plus isotropic ellipsoids (the large configuration).
+
+    The layer stack has a common seeded dip theta ~ U(0, 30) deg and azimuth phi, per layer
+    sigma_h = 10^U(-2, 1) S/m and anisotropy ratio r ~ U(1, 10) with sigma_v = sigma_h / r, rotated into
+    the tool frame by Appendix C. A fault plane (dip U(50, 80) deg, random strike, through a point in the
+    inner half of the grid) offsets the stack: on its hanging-wall side the layers are displaced
+    vertically by a throw U(2, 8) m. Ellipsoids: centres uniform in the inner 80 %, semi-axes U(1, 4) m,
+    random orientation, isotropic sigma = 10^U(-2, 1) S/m.
+    """
+    rng = np.random.default_rng(seed)
+    theta = np.deg2rad(rng.uniform(0.0, dip_max_deg))
+    phi = rng.uniform(0.0, 2.0 * np.pi)
+    nrm = np.array([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)])
+    half = 0.5 * grid.h * np.array([grid.nx, grid.ny, grid.nz])
+    reach = float(np.abs(nrm) @ half)
+    iface = np.sort(rng.uniform(-0.8 * reach, 0.8 * reach, n_layers - 1))
+    sh = _log_uniform(rng, -2.0, 1.0, n_layers)
+    sv = sh / rng.uniform(1.0, ratio_max, n_layers)
+    fdip, fstrike = np.deg2rad(rng.uniform(50.0, 80.0)), rng.uniform(0.0, 2.0 * np.pi)
+    fnrm = np.array([np.sin(fdip) * np.cos(fstrike), np.sin(fdip) * np.sin(fstrike), np.cos(fdip)])
+    lo = np.array(grid.origin)
+    ext = grid.h * np.array([grid.nx, grid.ny, grid.nz])
+    fpt = lo + ext * rng.uniform(0.25, 0.75, 3)
+    throw = rng.uniform(2.0, 8.0)
+    xc, yc, zc = grid.centres()
+    X, Y, Z = xc[None, None, :], yc[None, :, None], zc[:, None, None]
+    hanging = ((X - fpt[0]) * fnrm[0] + (Y - fpt[1]) * fnrm[1] + (Z - fpt[2]) * fnrm[2]) > 0.0
+    dist = X * nrm[0] + Y * nrm[1] + Z * nrm[2] - np.where(hanging, throw * nrm[2], 0.0)
+    layer = np.searchsorted(iface, dist)
+    del dist, hanging
+    s6 = ti_tensor(sh[layer], sv[layer], theta, phi)
+    del layer
+    for _ in range(n_ellipsoids):
+        c = lo + ext * rng.uniform(0.1, 0.9, 3)
+        ax = rng.uniform(1.0, 4.0, 3)
+        rot = _random_rotation(rng)
+        sig = _log_uniform(rng, -2.0, 1.0)
+        # only the bounding box of the ellipsoid is evaluated
+        i0 = [max(0, int(np.floor((c[a] - ax.max() - lo[a]) / grid.h))) for a in range(3)]
+        i1 = [min(n, int(np.ceil((c[a] + ax.max() - lo[a]) / grid.h)) + 1)
+              for a, n in enumerate((grid.nx, grid.ny, grid.nz))]
+        Zb, Yb, Xb = np.meshgrid(zc[i0[2]:i1[2]], yc[i0[1]:i1[1]], xc[i0[0]:i1[0]], indexing="ij")
+        d = np.stack([Xb - c[0], Yb - c[1], Zb - c[2]], axis=-1) @ rot  # body-frame coordinates
+        inside = np.sum((d / ax) ** 2, axis=-1) <= 1.0
+        box = s6[i0[2]:i1[2], i0[1]:i1[1], i0[0]:i1[0]]
+        box[inside, :3] = sig
+        box[inside, 3:] = 0.0
+    return s6
+
+
+_C5_CACHE: dict = {}
+
+
+def config5(seed: int = 0, position: int = 0, n_positions: int = 16, scale: int = 1) -> Workload:
+    """Large DD: 256x256x512 voxels of 0.25 m (33.5 M cells, 100.7 M complex unknowns) split into 8
+    sub-domains of 256x256x64 along z, block Jacobi; 7 dipping TI layers offset by a fault plus 5
+    ellipsoids (faulted_ti_with_ellipsoids); coaxial z-dipole tool at one of 16 positions along the z
+    axis, 2 m apart and centred on the grid (receivers 0.5/1/2 m above the transmitter); f = 2 MHz,
+    sigma0 = 0.1 S/m, tol 1e-6. The model is the same for every position (one set_contrast serves the
+    16 solves). ``scale`` > 1 divides every grid dimension and the position spacing (same cell size)."""
+    nx, ny, nz = 256 // scale, 256 // scale, 512 // scale
+    g = centred_grid(nx, ny, nz, 0.25)
+    key = (seed, scale)
+    if key not in _C5_CACHE:
+        _C5_CACHE.clear()
+        _C5_CACHE[key] = faulted_ti_with_ellipsoids(g, seed)
+    spacing = 2.0 / scale
+    zt = spacing * (position - 0.5 * (n_positions - 1))
+    src = [Dipole((0.0, 0.0, zt), (0.0, 0.0, 1.0))]
+    rx = np.array([[0.0, 0.0, zt + s] for s in (0.5, 1.0, 2.0)], dtype=np.float64)
+    split = [k * (nz // 8) for k in range(9)]
+    name = (f"DD {nx}x{ny}x{nz} @0.25 m, 8 blocks Jacobi, 7 faulted TI layers + 5 ellipsoids, "
+            f"position {position}/{n_positions}, 2 MHz")
+    return Workload(name, g, 0.1, 2.0e6, _C5_CACHE[key], src, rx, z_split=split, tol=1e-6, restart=40)
+
+
 @dataclass
 class Formation:
     """A layered earth model in global coordinates (z up) in the style of the paper's logging example
