@@ -42,6 +42,15 @@ template <typename V> __host__ __device__ __forceinline__ V cmul_conjb(V a, V b)
   return r;
 }
 template <typename V> __host__ __device__ __forceinline__ V czero() { V r; r.x = 0; r.y = 0; return r; }
+// y + a, or y - a when neg
+__device__ __forceinline__ float2 add_signed(float2 y, bool neg, float2 a) {
+  const float s = neg ? -1.f : 1.f;
+  return make_float2(fmaf(s, a.x, y.x), fmaf(s, a.y, y.y));
+}
+__device__ __forceinline__ double2 add_signed(double2 y, bool neg, double2 a) {
+  const double s = neg ? -1.0 : 1.0;
+  return make_double2(fma(s, a.x, y.x), fma(s, a.y, y.y));
+}
 // real scalar times complex
 template <typename S, typename V> __host__ __device__ __forceinline__ V cscale(S s, V a) {
   V r;
@@ -94,6 +103,7 @@ struct dfc {  // complex double-float, 16 bytes like double2
 template <> struct cplx_t<df> { using type = dfc; };
 __host__ __device__ __forceinline__ dfc operator+(dfc a, dfc b) { return dfc{a.x + b.x, a.y + b.y}; }
 __host__ __device__ __forceinline__ dfc operator-(dfc a, dfc b) { return dfc{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ dfc add_signed(dfc y, bool neg, dfc a) { return neg ? y - a : y + a; }
 __device__ __forceinline__ dfc to_c(double2 a, df) { return dfc{df(a.x), df(a.y)}; }
 __device__ __forceinline__ double2 to_c64(dfc a) { return make_double2(to_double(a.x), to_double(a.y)); }
 

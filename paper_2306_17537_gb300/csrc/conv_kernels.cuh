@@ -151,17 +151,21 @@ __global__ void __launch_bounds__(kThreads) k_lanes_fft(
 // back from [ot, ot + nzt). With os = ot = 0 this is a block's own convolution; with the whole-domain
 // spectra and os/ot the blocks' z offsets it is the interaction between two sub-domains.
 // The three forward spectra are kept in shared memory (one buffer per component, also used for that
-// component's FFT exchanges), so a thread holds one pencil in registers at a time: 128-thread blocks
-// with 48 KB of shared memory, four blocks per SM.
-template <typename T, int L, int WDIV = 1> struct P3Cfg {
+// component's FFT exchanges), so a thread holds one pencil in registers at a time. A block is W
+// neighbouring lanes kx (W = NT / TT for about NT threads): wider tiles give longer contiguous row
+// segments in B and in the Green octant, narrower ones more blocks per SM; the autotuner chooses.
+template <typename T, int L, int NT = 128> struct P3Cfg {
   static constexpr int TT = Plan<T, L>::TT;
-  static constexpr int W0 = 128 / TT / WDIV;
+  static constexpr int W0 = NT / TT;
   static constexpr int W = W0 < 1 ? 1 : (W0 > 32 ? 32 : W0);
+  static constexpr int NTH = W * TT;                 // threads launched per block
+  static constexpr int MINB = NTH >= 512 ? 1 : 512 / NTH;  // blocks per SM the register budget is set for
   // TMA staging of the input pencils needs box rows of a multiple of 16 bytes (W lanes per row)
   static constexpr bool kTmaOk = (W * (int)sizeof(C<T>)) % 16 == 0;
   static constexpr int BZ = L < 256 ? L : 256;  // rows per TMA box (the box limit is 256)
-  // spectra + 3 mbarriers + room to align the TMA destinations to 128 bytes
-  static constexpr size_t kTmaSmem = 3 * (size_t)L * W * sizeof(C<T>) + 64 + 128;
+  static constexpr size_t kSpecBytes = 3 * (size_t)L * W * sizeof(C<T>);
+  // spectra + 3 mbarriers + room to align the spectra (and TMA destinations) to 128 bytes
+  static constexpr size_t kSmem = kSpecBytes + 64 + 128;
 };
 
 // TMA: all three components' input pencils (W lanes x L positions, the zero padding and positions
@@ -169,25 +173,19 @@ template <typename T, int L, int WDIV = 1> struct P3Cfg {
 // asynchronous tensor copies issued at kernel start, so the loads of components 1 and 2 overlap the FFT
 // of component 0. Otherwise each component is loaded into registers just before its FFT. A staging
 // wait that exceeds its spin limit sets *err, waits (bounded) for the other copies and ends the block.
-template <typename T, int L, int WDIV, bool TMA>
-__global__ void __launch_bounds__(128, 4) k_p3_spectral(
+template <typename T, int L, int NT, bool TMA>
+__global__ void __launch_bounds__(P3Cfg<T, L, NT>::NTH, P3Cfg<T, L, NT>::MINB) k_p3_spectral(
     const C<T>* __restrict__ Bin, long in_cs, int nzs, int os, C<T>* __restrict__ Bout, long out_cs,
     int nzt, int ot, const C<T>* __restrict__ G, int Lx, int Ly, const C<T>* __restrict__ tw,
     const __grid_constant__ CUtensorMap tmap, int* __restrict__ err) {
-  using Cfg = P3Cfg<T, L, WDIV>;
+  using Cfg = P3Cfg<T, L, NT>;
   constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = Cfg::W;
   constexpr bool kTma = TMA && Cfg::kTmaOk;
-  C<T>* spec_base;
-  uint64_t* bar = nullptr;
-  if constexpr (kTma) {
-    extern __shared__ __align__(128) unsigned char p3_dyn[];
-    unsigned char* base = p3_dyn + ((128u - (smem_addr(p3_dyn) & 127u)) & 127u);
-    spec_base = reinterpret_cast<C<T>*>(base);
-    bar = reinterpret_cast<uint64_t*>(base + 3 * (size_t)L * W * sizeof(C<T>));
-  } else {
-    __shared__ C<T> p3_static[3 * L * W];
-    spec_base = p3_static;
-  }
+  extern __shared__ __align__(128) unsigned char p3_dyn[];
+  unsigned char* sbase = p3_dyn + ((128u - (smem_addr(p3_dyn) & 127u)) & 127u);
+  C<T>* spec_base = reinterpret_cast<C<T>*>(sbase);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sbase + Cfg::kSpecBytes);
+  (void)bar;
   auto spec = [spec_base](int c) { return spec_base + c * (L * W); };
   const int w = threadIdx.x, t = threadIdx.y;
   const int kx = blockIdx.x * W + w, ky = blockIdx.y;
@@ -240,39 +238,37 @@ __global__ void __launch_bounds__(128, 4) k_p3_spectral(
   // Green product at the thread's own frequencies (no other thread touches these slots).
   // The octant holds F[K_pq] for 0 <= k <= L/2 per axis; the full spectrum follows from the
   // parities of K (diagonal components even, K_pq odd along p and q): with s_a = +-1 the side of
-  // axis a, F[K_pq](k) = s_p s_q F[K_pq](|k|), so Y_p = s_p sum_q F_pq(|k|) (s_q J_q). Register m of a
+  // axis a, F[K_pq](k) = s_p s_q F[K_pq](|k|), so Y_p = sum_q s_p s_q F_pq(|k|) J_q: the diagonal terms
+  // carry no sign and the off-diagonal ones the products s_x s_y, s_x s_z, s_y s_z. Register m of a
   // pencil holds kz = t + TT*m, which lies in the lower half exactly when m < E/2 (the Nyquist
   // frequency kz = L/2, where the odd components vanish, may take either side).
-  {
+  if (act) {
     const int ox = Lx / 2 + 1, oy = Ly / 2 + 1;
     const long ocs = (long)(L / 2 + 1) * oy * ox, ozs = (long)oy * ox;
     const bool xlo = kx <= Lx / 2, ylo = ky <= Ly / 2;
     const int ix = xlo ? kx : Lx - kx, iy = ylo ? ky : Ly - ky;
+    const bool nxy = xlo != ylo;
     const C<T>* gb = G + (long)iy * ox + ix;
     LaneSM<T, W> s0{spec(0) + w}, s1{spec(1) + w}, s2{spec(2) + w};
-    if (act) {
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        constexpr int half = E / 2;
-        const bool zlo = (E == 1) || (m < half);
-        const int kz = t + TT * m, iz = zlo ? kz : L - kz;
-        const C<T>* g = gb + iz * ozs;
-        const C<T> gxx = ldgv(g), gyy = ldgv(g + ocs), gzz = ldgv(g + 2 * ocs);
-        const C<T> gxy = ldgv(g + 3 * ocs), gxz = ldgv(g + 4 * ocs), gyz = ldgv(g + 5 * ocs);
-        C<T> j0 = s0.ld(kz), j1 = s1.ld(kz), j2 = s2.ld(kz);
-        if (!xlo) j0 = mk<T>(-j0.x, -j0.y);
-        if (!ylo) j1 = mk<T>(-j1.x, -j1.y);
-        if (!zlo) j2 = mk<T>(-j2.x, -j2.y);
-        C<T> y0 = cmul(gxx, j0) + cmul(gxy, j1) + cmul(gxz, j2);
-        C<T> y1 = cmul(gxy, j0) + cmul(gyy, j1) + cmul(gyz, j2);
-        C<T> y2 = cmul(gxz, j0) + cmul(gyz, j1) + cmul(gzz, j2);
-        if (!xlo) y0 = mk<T>(-y0.x, -y0.y);
-        if (!ylo) y1 = mk<T>(-y1.x, -y1.y);
-        if (!zlo) y2 = mk<T>(-y2.x, -y2.y);
-        s0.st(kz, y0);
-        s1.st(kz, y1);
-        s2.st(kz, y2);
-      }
+    auto product = [&](int kz, int iz, bool nxz, bool nyz) {
+      const C<T>* g = gb + iz * ozs;
+      const C<T> gxx = ldgv(g), gyy = ldgv(g + ocs), gzz = ldgv(g + 2 * ocs);
+      const C<T> gxy = ldgv(g + 3 * ocs), gxz = ldgv(g + 4 * ocs), gyz = ldgv(g + 5 * ocs);
+      const C<T> j0 = s0.ld(kz), j1 = s1.ld(kz), j2 = s2.ld(kz);
+      s0.st(kz, add_signed(add_signed(cmul(gxx, j0), nxy, cmul(gxy, j1)), nxz, cmul(gxz, j2)));
+      s1.st(kz, add_signed(add_signed(cmul(gyy, j1), nxy, cmul(gxy, j0)), nyz, cmul(gyz, j2)));
+      s2.st(kz, add_signed(add_signed(cmul(gzz, j2), nxz, cmul(gxz, j0)), nyz, cmul(gyz, j1)));
+    };
+    constexpr int half = E == 1 ? 1 : E / 2;
+#pragma unroll 4
+    for (int m = 0; m < half; ++m) {  // lower half of kz: s_z = +1
+      const int kz = t + TT * m;
+      product(kz, kz, !xlo, !ylo);
+    }
+#pragma unroll 4
+    for (int m = half; m < E; ++m) {  // upper half: s_z = -1
+      const int kz = t + TT * m;
+      product(kz, L - kz, xlo, ylo);
     }
   }
   // inverse z-FFT of each component and crop

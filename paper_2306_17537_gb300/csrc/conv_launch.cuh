@@ -4,7 +4,6 @@
 #pragma once
 #include "conv.cuh"
 #include "conv_kernels.cuh"
-#include "conv_p3w.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -149,12 +148,31 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // TMA = true stages the input pencils with tensor copies when the tile allows it (P3Cfg::kTmaOk) and
 // the CUDA driver provides the tensor-map encoder; otherwise the same tile runs with register loads.
-template <typename T, int N, int WDIV, bool TMA>
+// Every tile keeps its spectra in dynamic shared memory (above the 48 KB default for the wider tiles).
+template <typename T, int N, int NT, bool TMA>
+static cudaError_t p3_run(const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt, int ot,
+                          const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err, const CUtensorMap& map,
+                          cudaStream_t s) {
+  using Cfg = P3Cfg<T, N, NT>;
+  static std::once_flag attr;
+  static cudaError_t ae = cudaSuccess;
+  std::call_once(attr, [] {
+    if (Cfg::kSmem > 48 * 1024)
+      ae = cudaFuncSetAttribute(k_p3_spectral<T, N, NT, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg::kSmem);
+  });
+  if (ae != cudaSuccess) return ae;
+  dim3 blk(Cfg::W, Plan<T, N>::TT), grd((unsigned)((Lx + Cfg::W - 1) / Cfg::W), (unsigned)Ly);
+  k_p3_spectral<T, N, NT, TMA><<<grd, blk, Cfg::kSmem, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw,
+                                                            map, err);
+  return cudaGetLastError();
+}
+
+template <typename T, int N, int NT, bool TMA>
 static cudaError_t p3_launch(const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt, int ot,
                              const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err, cudaStream_t s) {
-  using Cfg = P3Cfg<T, N, WDIV>;
+  using Cfg = P3Cfg<T, N, NT>;
   constexpr int W = Cfg::W;
-  dim3 blk(W, Plan<T, N>::TT), grd((unsigned)((Lx + W - 1) / W), (unsigned)Ly);
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
   if constexpr (TMA && Cfg::kTmaOk) {
@@ -170,37 +188,10 @@ static cudaError_t p3_launch(const C<T>* Bin, long in_cs, int nzs, int os, C<T>*
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-      static std::once_flag attr;
-      cudaError_t ae = cudaSuccess;
-      std::call_once(attr, [&] {
-        ae = cudaFuncSetAttribute(k_p3_spectral<T, N, WDIV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)Cfg::kTmaSmem);
-      });
-      if (ae != cudaSuccess) return ae;
-      k_p3_spectral<T, N, WDIV, true><<<grd, blk, Cfg::kTmaSmem, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G,
-                                                                      Lx, Ly, tw, map, err);
-      return cudaGetLastError();
+      return p3_run<T, N, NT, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, map, s);
     }
   }
-  k_p3_spectral<T, N, WDIV, false><<<grd, blk, 0, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw,
-                                                       map, err);
-  return cudaGetLastError();
-}
-
-// Variant 4: warp-resident pencils with the spectra in registers (k_p3_warp), complex64 and L <= 512.
-template <typename T, int N>
-static cudaError_t p3_warp_launch(const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt,
-                                  int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, cudaStream_t s) {
-  if constexpr (std::is_same<T, float>::value && N <= 512) {
-    using Cfg = P3WCfg<N>;
-    if (in_cs > INT32_MAX || out_cs > INT32_MAX || 3L * in_cs > INT32_MAX || 3L * out_cs > INT32_MAX)
-      return cudaErrorInvalidValue;
-    dim3 blk(32 * Cfg::NW), grd((unsigned)((Lx + Cfg::LANES - 1) / Cfg::LANES), (unsigned)Ly);
-    k_p3_warp<N><<<grd, blk, 0, s>>>(Bin, (int)in_cs, nzs, os, Bout, (int)out_cs, nzt, ot, G, Lx, Ly, tw);
-    return cudaGetLastError();
-  } else {
-    return p3_launch<T, N, 1, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, nullptr, s);
-  }
+  return p3_run<T, N, NT, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, map, s);
 }
 
 template <typename T>
@@ -208,14 +199,15 @@ cudaError_t ConvLaunch<T>::p3(int L, int variant, const C<T>* Bin, long in_cs, i
                               long out_cs, int nzt, int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err,
                               cudaStream_t s) {
   switch (L) {
-#define IE_CASE(N)                                                                                                 \
-  case N:                                                                                                          \
-    switch (variant) {                                                                                             \
-      case 1: return p3_launch<T, N, 2, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
-      case 2: return p3_launch<T, N, 1, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
-      case 3: return p3_launch<T, N, 2, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
-      case 4: return p3_warp_launch<T, N>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, s);          \
-      default: return p3_launch<T, N, 1, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
+#define IE_CASE(N)                                                                                                  \
+  case N:                                                                                                           \
+    switch (variant) {                                                                                              \
+      case 1: return p3_launch<T, N, 64, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
+      case 2: return p3_launch<T, N, 128, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
+      case 3: return p3_launch<T, N, 64, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);   \
+      case 4: return p3_launch<T, N, 256, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
+      case 5: return p3_launch<T, N, 256, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
+      default: return p3_launch<T, N, 128, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);\
     }
     IE_FOR_EACH_L(IE_CASE)
 #undef IE_CASE

@@ -93,15 +93,6 @@ template <typename T, int W> struct LaneSM {
   __device__ __forceinline__ void st(int i, C<T> x) const { base[row(i) * W] = x; }
 };
 
-// Barrier between the exchange steps of a pencil: the whole block when a pencil's threads span
-// several warps, the warp alone when every pencil lives inside one warp (no block barrier at all).
-struct BlockSync {
-  __device__ __forceinline__ static void sync() { __syncthreads(); }
-};
-struct WarpSync {
-  __device__ __forceinline__ static void sync() { __syncwarp(); }
-};
-
 template <typename T, int SIGN>
 __device__ __forceinline__ C<T> twiddle(const C<T>* __restrict__ tw, int idx) {
   C<T> w = ldgv(tw + idx);
@@ -109,7 +100,7 @@ __device__ __forceinline__ C<T> twiddle(const C<T>* __restrict__ tw, int idx) {
   return w;
 }
 
-template <typename T, int L, int SIGN, int NS, class SM, class SYNC = BlockSync> struct Stages {
+template <typename T, int L, int SIGN, int NS, class SM> struct Stages {
   static constexpr int E = Plan<T, L>::E;
   static constexpr int TT = Plan<T, L>::TT;
   static constexpr int REM = L / NS;
@@ -128,7 +119,7 @@ template <typename T, int L, int SIGN, int NS, class SM, class SYNC = BlockSync>
       for (int b = 0; b < NB; ++b)
 #pragma unroll
         for (int r = 0; r < R; ++r) x[b][r] = sm.ld(t + TT * b + r * (L / R));
-      SYNC::sync();
+      __syncthreads();
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -154,19 +145,18 @@ template <typename T, int L, int SIGN, int NS, class SM, class SYNC = BlockSync>
 #pragma unroll
         for (int r = 0; r < R; ++r) sm.st(base + r * NS, x[b][r]);
       }
-      SYNC::sync();
-      Stages<T, L, SIGN, (LAST ? NS : NS * R), SM, SYNC>::run(v, t, sm, tw);
+      __syncthreads();
+      Stages<T, L, SIGN, (LAST ? NS : NS * R), SM>::run(v, t, sm, tw);
     }
   }
 };
 
 // Forward (SIGN = -1) or unnormalised inverse (SIGN = +1) DFT of one pencil held as described above.
-// Every thread of the block (SYNC = BlockSync) or of the warp (WarpSync, all of the pencil's threads
-// in one warp) must call it: it contains the barrier between exchange steps when L > E.
-template <typename T, int L, int SIGN, class SM, class SYNC = BlockSync>
+// Every thread of the block must call it (it contains __syncthreads when L > E).
+template <typename T, int L, int SIGN, class SM>
 __device__ __forceinline__ void pencil_fft(C<T> (&v)[Plan<T, L>::E], int t, const SM& sm,
                                            const C<T>* __restrict__ tw) {
-  Stages<T, L, SIGN, 1, SM, SYNC>::run(v, t, sm, tw);
+  Stages<T, L, SIGN, 1, SM>::run(v, t, sm, tw);
 }
 
 }  // namespace ie

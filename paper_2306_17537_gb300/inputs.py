@@ -212,11 +212,13 @@ def faulted_ti_with_ellipsoids(grid: Grid, seed: int, n_layers: int = 7, ratio_m
     """Dipping TI layers offset by a planar fault, plus isotropic ellipsoids (the large configuration).
 
     The layer stack has a common seeded dip theta ~ U(0, 30) deg and azimuth phi, per layer
-    sigma_h = 10^U(-2, 1) S/m and anisotropy ratio r ~ U(1, 10) with sigma_v = sigma_h / r, rotated into
-    the tool frame by Appendix C. A fault plane (dip U(50, 80) deg, random strike, through a point in the
-    inner half of the grid) offsets the stack: on its hanging-wall side the layers are displaced
-    vertically by a throw U(2, 8) m. Ellipsoids: centres uniform in the inner 80 %, semi-axes U(1, 4) m,
-    random orientation, isotropic sigma = 10^U(-2, 1) S/m.
+    sigma_h = 10^U(-1.5, 0.3) S/m (0.03 - 2 S/m, the range of the logging formation of Section 3.3) and
+    anisotropy ratio r ~ U(1, 10) with sigma_v = sigma_h / r, rotated into the tool frame by Appendix C.
+    A fault plane (dip U(50, 80) deg, random strike, through a point in the inner half of the grid)
+    offsets the stack: on its hanging-wall side the layers are displaced vertically by a throw U(2, 8) m.
+    Ellipsoids: centres uniform in the inner 80 %, semi-axes U(1, 4) m, random orientation, isotropic
+    sigma = 10^U(-2, 0.3) S/m. (At 2 MHz a 10 S/m layer has a skin depth of 0.11 m, under half a
+    0.25 m cell: the conductivities stop at 2 S/m, where it is 0.25 m.)
     """
     rng = np.random.default_rng(seed)
     theta = np.deg2rad(rng.uniform(0.0, dip_max_deg))
@@ -225,7 +227,7 @@ def faulted_ti_with_ellipsoids(grid: Grid, seed: int, n_layers: int = 7, ratio_m
     half = 0.5 * grid.h * np.array([grid.nx, grid.ny, grid.nz])
     reach = float(np.abs(nrm) @ half)
     iface = np.sort(rng.uniform(-0.8 * reach, 0.8 * reach, n_layers - 1))
-    sh = _log_uniform(rng, -2.0, 1.0, n_layers)
+    sh = _log_uniform(rng, -1.5, 0.3, n_layers)
     sv = sh / rng.uniform(1.0, ratio_max, n_layers)
     fdip, fstrike = np.deg2rad(rng.uniform(50.0, 80.0)), rng.uniform(0.0, 2.0 * np.pi)
     fnrm = np.array([np.sin(fdip) * np.cos(fstrike), np.sin(fdip) * np.sin(fstrike), np.cos(fdip)])
@@ -245,7 +247,7 @@ def faulted_ti_with_ellipsoids(grid: Grid, seed: int, n_layers: int = 7, ratio_m
         c = lo + ext * rng.uniform(0.1, 0.9, 3)
         ax = rng.uniform(1.0, 4.0, 3)
         rot = _random_rotation(rng)
-        sig = _log_uniform(rng, -2.0, 1.0)
+        sig = _log_uniform(rng, -2.0, 0.3)
         # only the bounding box of the ellipsoid is evaluated
         i0 = [max(0, int(np.floor((c[a] - ax.max() - lo[a]) / grid.h))) for a in range(3)]
         i1 = [min(n, int(np.ceil((c[a] + ax.max() - lo[a]) / grid.h)) + 1)
