@@ -1,22 +1,25 @@
 #!/usr/bin/env python3
-"""Benchmark of the IE forward model (one solve = one step) on the 128x128x256 two-sub-domain workload.
+"""Benchmark of the IE forward model: tool-position solves per second at e <= 1e-6 (eq. 9, FP64-verified).
 
-Workload (the paper's logging window 1 shape, Section 3.3): 128 x 128 x 256 cells of 0.25 m split
-into two 128^3 sub-domains along z, block Gauss-Seidel with the adaptive sub-domain tolerance e/10
-(Algorithm 1), each block solved by GMRES on the contraction form of the IE operator (the default;
-``--operator conventional`` runs the paper's conventional form, which the line also reports as a
-variant), complex64 FFT convolution and Krylov vectors with FP64 whole-grid residual and
-refinement, target e <= 1e-6 (eq. 9, the conventional residual) verified in FP64; five dipping TI layers (anisotropy ratio
-1-10, Appendix C rotation) plus two isotropic ellipsoids, seeded; coaxial z magnetic dipole with
-receivers at 0.5/1/2 m; f = 400 kHz, sigma0 = 0.1 S/m. Synthetic data: the paper's formations
-exist only in figures.
+Default workload (`--workload c5`, the largest single-GPU configuration): 256 x 256 x 512 cells of
+0.25 m (33.5 M cells, 100.7 M complex unknowns) split into 8 sub-domains of 256 x 256 x 64 along the
+tool axis; 7 dipping TI layers offset by a fault plus 5 isotropic ellipsoids (seeded); coaxial z
+magnetic dipole with receivers 0.5/1/2 m above it at 16 positions 2 m apart along the axis; 2 MHz;
+sigma0 = 0.1 S/m. Solver: block Jacobi over the 8 sub-domains with all block solves in flight together
+(concurrent worker streams), used as the preconditioner of a flexible GMRES(20) outer iteration on the
+whole-grid system (the Krylov acceleration the paper proposes for its fixed-point sweeps), block GMRES
+on the contraction form of the operator, complex64 FFT convolution and Krylov vectors, FP64-accurate
+(double-float) whole-grid residuals. One step = one tool position's solve (incident field, DD solve,
+receivers); the model is uploaded (ie_set_contrast_dev / ie_set_contrast) at the first step of every
+round of 16 positions, inside the timed region. Green spectra (ie_create) depend only on grid, cell
+size, background and frequency and are computed once before timing, as the paper precomputes them
+(Section 2.2). Inputs (fields 1.6 GB, Krylov bases tens of GB) are far larger than the 129 MB L2.
 
-One step = ie_set_contrast_dev + ie_solve (incident field, Algorithm 1, receivers). The Green
-spectra (ie_create) depend only on the grid, cell size, background and frequency and are computed
-once before the timed region, as the paper precomputes them (Section 2.2). Inputs (fields 200 MB,
-Krylov basis 1.5 GB per sub-domain solve) are larger than the 129 MB L2.
+`--workload c2`: the 128 x 128 x 256 two-sub-domain block Gauss-Seidel configuration (Algorithm 1 with
+the adaptive tolerance, contraction form), one tool position, 400 kHz; it is also timed as a variant of
+the default line.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}] [--workload c5|c2]
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
@@ -36,12 +39,55 @@ if ROOT not in sys.path:
 
 METRIC = "IE forward solves/sec at 1e-6 rel. residual; matvec HBM GB/s vs peak"
 UNIT = "solves/s"
-WORKLOAD = "DD 128x128x256 @0.25 m, 2 sub-domains block Gauss-Seidel adaptive (GS-A), 5 dipping TI layers + 2 ellipsoids, 1 coaxial tool position, 400 kHz, tol 1e-6"
-# Sub-domain operator applications of one solve of this workload per operator form (GMRES steps,
-# restart residuals and the 10 interaction updates of the GS-A solve, as the GB300 arm counts them) and
-# whole-grid applications (one FP64 residual per sweep plus the initial one), used only to scale the
-# CPU oracle sample of the reference arm, which runs without the GB300 arm, to solves/s.
-REF_APPLICATIONS_PER_SOLVE = {"contraction": (260, 11), "conventional": (650, 11)}
+POSITIONS_C5 = 16
+
+
+class BenchWorkload:
+    """One benchmark configuration: the seeded model, the tool positions a step cycles through, the DD
+    mode and solver options (as plain values; the GB300 arm turns them into ie_opts), the sub-domain
+    whose operator bandwidth is reported, and a one-line description."""
+
+    def __init__(self, key: str, seed: int, scale: int = 1, operator: str = "contraction", restart=None):
+        from paper_2306_17537_gb300 import inputs
+
+        self.key = key
+        contraction = operator == "contraction"
+        if key == "c5":
+            self.items = [inputs.config5(seed, p, n_positions=POSITIONS_C5, scale=scale) for p in range(POSITIONS_C5)]
+            wl = self.items[0]
+            self.dd = "jacobi"
+            self.opts = dict(z_split=wl.z_split, restart=restart or wl.restart, max_inner=4000, max_outer=60,
+                             contraction=contraction, concurrent_blocks=True, outer_krylov=True, outer_restart=20,
+                             outer_inner_tol=0.1)
+            g = wl.grid
+            self.description = (f"DD {g.nx}x{g.ny}x{g.nz} @0.25 m, 8 sub-domains block Jacobi (all block solves in "
+                                f"flight together) preconditioning flexible GMRES(20), 7 faulted TI layers + 5 "
+                                f"ellipsoids, {POSITIONS_C5} tool positions, 2 MHz, tol 1e-6")
+            self.dd_text = "flexible GMRES(20) outer iteration, preconditioner: one concurrent block-Jacobi sweep (block tol 0.1)"
+        elif key == "c2":
+            self.items = [inputs.config2(seed, scale=scale)]
+            wl = self.items[0]
+            self.dd = "gs"
+            self.opts = dict(z_split=wl.z_split, restart=restart or wl.restart, max_inner=4000, max_outer=60,
+                             contraction=contraction)
+            g = wl.grid
+            self.description = (f"DD {g.nx}x{g.ny}x{g.nz} @0.25 m, 2 sub-domains block Gauss-Seidel adaptive (GS-A), "
+                                f"5 dipping TI layers + 2 ellipsoids, 1 coaxial tool position, 400 kHz, tol 1e-6")
+            self.dd_text = "block Gauss-Seidel fixed-point sweeps (Algorithm 1), adaptive block tol e/10"
+        else:
+            raise ValueError(key)
+        self.grid = wl.grid
+        self.sigma6 = wl.sigma6
+        self.sigma0, self.freq, self.tol = wl.sigma0, wl.freq, wl.tol
+        self.split = wl.z_split
+        self.block = (self.split[0], self.split[1])  # the sub-domain whose operator is timed alone
+
+    def item(self, step: int):
+        return self.items[step % len(self.items)]
+
+    def uploads_model(self, step: int) -> bool:
+        """The model is (re)uploaded at the first position of every round of positions."""
+        return step % len(self.items) == 0
 
 
 def parse():
@@ -56,6 +102,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--operator", default="contraction", choices=["contraction", "conventional"],
                     help="operator form GMRES iterates on inside the sub-domain solves")
+    ap.add_argument("--workload", default="c5", choices=["c5", "c2"])
     return ap.parse_args()
 
 
@@ -166,25 +213,37 @@ def traffic_record(kernel_class: str):
 
 
 # ------------------------------------------------------------------------------------ CPU oracle
-def oracle_block_sample(wl, z0, nz, n_apply=1, contraction=True):
-    """Time the CPU oracle's operator of one sub-domain (the contraction or the conventional form):
-    spectra setup + n_apply applications."""
+def oracle_block_sample(bw, nz, n_apply=1, contraction=True):
+    """Time the CPU oracle's operator of one z slab of `nz` planes at the bottom of the model (the
+    contraction or the conventional form): spectra setup + n_apply applications (seconds each)."""
     import numpy as np
 
     from oracle import contraction as oc
     from oracle import operator as oop
 
+    g = bw.grid
+    s6 = bw.sigma6[:nz]
     t0 = time.perf_counter()
     if contraction:
-        op = oc.ContractionOperator(wl.sigma6[z0:z0 + nz], wl.grid.h, wl.freq, wl.sigma0)
+        op = oc.ContractionOperator(s6, g.h, bw.freq, bw.sigma0)
     else:
-        op = oop.FFTOperator(oop.contrast(wl.sigma6[z0:z0 + nz], wl.sigma0), wl.grid.h, wl.freq, wl.sigma0)
+        op = oop.FFTOperator(oop.contrast(s6, bw.sigma0), g.h, bw.freq, bw.sigma0)
     t1 = time.perf_counter()
-    x = np.ones((3, nz, wl.grid.ny, wl.grid.nx), dtype=np.complex128)
+    x = np.ones((3, nz, g.ny, g.nx), dtype=np.complex128)
     for _ in range(n_apply):
         x = op(x)
     t2 = time.perf_counter()
     return t1 - t0, (t2 - t1) / n_apply
+
+
+def padded_volume(g, nz):
+    """Padded FFT volume of a slab of nz planes (the pass model's cost scale of one application)."""
+    def p2(n):
+        v = 1
+        while v < 2 * n:
+            v *= 2
+        return v
+    return p2(g.nx) * p2(g.ny) * p2(nz)
 
 
 def cpu_cores():
@@ -229,165 +288,156 @@ def c1_full_solves(ie, torch, dev, stream, reps=3):
 
 
 # ------------------------------------------------------------------------------------ GB300 arm
+def timed(stream, torch, dev, fn, steps, world, dist):
+    """Run fn(k) for k = 0..steps-1 between CUDA events on `stream` (barrier + synchronize on both
+    sides); returns (ms, results)."""
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = [fn(k) for k in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    return e0.elapsed_time(e1), res
+
+
 def run_gb300(args):
     import numpy as np
     import torch
     import torch.distributed as dist
 
-    from paper_2306_17537_gb300 import ie, inputs
+    from paper_2306_17537_gb300 import ie
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    # weak scaling: every rank solves its own tool position (independent model seed), no data exchange
-    wl = inputs.config2(rank_seed(args.seed, rank), scale=args.scale)
-    g = wl.grid
-    t_setup0 = time.perf_counter()
-    ctx = ie.Context(g, g.h, wl.sigma0, wl.freq)
+    # weak scaling: every rank solves its own seeded model (independent problems), no data exchange
+    bw = BenchWorkload(args.workload, rank_seed(args.seed, rank), args.scale, args.operator, args.restart)
+    g = bw.grid
+    dd_mode = {"jacobi": ie.IE_DD_JACOBI, "gs": ie.IE_DD_GAUSS_SEIDEL}[bw.dd]
     stream = torch.cuda.current_stream(dev)
+    t_setup0 = time.perf_counter()
+    ctx = ie.Context(g, g.h, bw.sigma0, bw.freq)
     ctx.set_stream(stream)
     setup_s = time.perf_counter() - t_setup0
-    s6_dev = torch.from_numpy(np.ascontiguousarray(wl.sigma6)).to(dev)
-    if args.restart:
-        wl.restart = args.restart
-    contraction = args.operator == "contraction"
-    opts = ie.make_opts(z_split=wl.z_split, restart=wl.restart, precision=ie.IE_PREC_MIXED, max_inner=4000,
-                        max_outer=60, contraction=contraction)
-    src, rx = wl.sources, wl.receivers
+    s6_dev = torch.from_numpy(np.ascontiguousarray(bw.sigma6)).to(dev)
+    opts = ie.make_opts(precision=ie.IE_PREC_MIXED, **bw.opts)
 
-    def step_dev():
-        ctx.set_contrast_dev(s6_dev)
-        return ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, opts)
+    def step_dev(k):
+        if bw.uploads_model(k):
+            ctx.set_contrast_dev(s6_dev)
+        it = bw.item(k)
+        return ctx.solve(it.sources, it.receivers, dd_mode, bw.tol, opts)
 
-    for _ in range(args.warmup):
-        H, info, st = step_dev()
+    for k in range(args.warmup):
+        step_dev(k)
     # ----------------------------------------------------------------- timed region (device inputs)
     # no launch accounting inside: the per-kernel breakdown comes from a separate profiled pass below
     ctx.profile_enable(False)
     clocks = ClockSampler(local)
     clocks.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    results = []
-    for _ in range(args.steps):
-        results.append(step_dev())
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    t_ms, results = timed(stream, torch, dev, step_dev, args.steps, world, dist)
     clk = clocks.stop()
-    t_ms = ev0.elapsed_time(ev1)
     t_ms_max = max_over_ranks(t_ms, dev)
-    H, _, st = results[-1]
     infos = [r[1] for r in results]
-    failed = [k for k, (_, inf, stk) in enumerate(results)
-              if stk != ie.IE_OK or not (inf.final_rel_residual <= wl.tol)]
+    failed = [k for k, (_, inf, stk) in enumerate(results) if stk != ie.IE_OK or not (inf.final_rel_residual <= bw.tol)]
     value = job_throughput(args.steps, world, t_ms_max) if not failed else None
+    H, _, st = results[-1]
     # ----------------------------------------------------------------- end to end (host buffers)
-    # the same number of steps as the device-input region; inputs come from pinned host memory and
-    # the receiver fields go back to the host every step
-    s6_pin = torch.from_numpy(np.ascontiguousarray(wl.sigma6)).pin_memory()
-    s6_host = s6_pin.numpy()
-    e2e_steps = args.steps
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    e2e_ok = True
-    for _ in range(e2e_steps):
-        ctx.set_contrast(s6_host)
-        H2, info2, st2 = ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, opts)
-        e2e_ok = e2e_ok and st2 == ie.IE_OK and info2.final_rel_residual <= wl.tol
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_value = job_throughput(e2e_steps, world, max_over_ranks(e0.elapsed_time(e1), dev)) if e2e_ok else None
-    h2d = s6_host.nbytes + rx.nbytes + 48 * len(src)
-    d2h = H2.nbytes
+    # the same steps with every input from pinned host memory (the model at the first position of a
+    # round, sources and receivers every step) and the receiver fields back on the host every step
+    s6_host = torch.from_numpy(np.ascontiguousarray(bw.sigma6)).pin_memory().numpy()
+    h2d_total, d2h_total = 0, 0
+
+    def step_host(k):
+        nonlocal h2d_total, d2h_total
+        if bw.uploads_model(k):
+            ctx.set_contrast(s6_host)
+            h2d_total += s6_host.nbytes
+        it = bw.item(k)
+        r = ctx.solve(it.sources, it.receivers, dd_mode, bw.tol, opts)
+        h2d_total += it.receivers.nbytes + 48 * len(it.sources)
+        d2h_total += r[0].nbytes
+        return r
+
+    e_ms, e_res = timed(stream, torch, dev, step_host, args.steps, world, dist)
+    e2e_ok = all(stk == ie.IE_OK and inf.final_rel_residual <= bw.tol for _, inf, stk in e_res)
+    e2e_value = job_throughput(args.steps, world, max_over_ranks(e_ms, dev)) if e2e_ok else None
     # ----------------------------------------------------------------- profiled pass (per-kernel times)
-    # per-launch CUDA events on the context stream around every kernel of the same solves; these
+    # per-launch CUDA events on the launching streams around every kernel of the same solves; these
     # steps are not part of `value`
     prof_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize(dev)
     ctx.profile_enable(True)
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    for _ in range(prof_steps):
-        step_dev()
-    p1.record(stream)
-    torch.cuda.synchronize(dev)
+    p_ms, _ = timed(stream, torch, dev, step_dev, prof_steps, 1, dist)
     prof = ctx.profile_read()
     ctx.profile_enable(False)
-    prof_ms = p0.elapsed_time(p1)
-    # ----------------------------------------------------------------- the other operator form
-    other = "conventional" if contraction else "contraction"
-    vopts = ie.make_opts(z_split=wl.z_split, restart=wl.restart, precision=ie.IE_PREC_MIXED, max_inner=4000,
-                         max_outer=60, contraction=not contraction)
-    ctx.set_contrast_dev(s6_dev)
-    ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, vopts)
+    # ----------------------------------------------------------------- variants (a step or a few each)
+    variants = {}
+
+    def variant(name, vopts, steps, note, ctx_=None, items=None, dd=None, reupload=True):
+        c_ = ctx_ or ctx
+        its_ = items or bw.items
+        dd_ = dd if dd is not None else dd_mode
+        vo = ie.make_opts(precision=ie.IE_PREC_MIXED, **vopts)
+
+        def vstep(k):
+            if reupload and k == 0:
+                c_.set_contrast_dev(s6_dev) if c_ is ctx else None
+            it = its_[k % len(its_)]
+            return c_.solve(it.sources, it.receivers, dd_, it.tol, vo)
+
+        vstep(0)
+        v_ms, vres = timed(stream, torch, dev, vstep, steps, world, dist)
+        Hv, vinfo, vst = vres[-1]
+        ref = results[(steps - 1) % len(results)][0] if c_ is ctx else None
+        variants[name] = {"note": note, "value": round(job_throughput(steps, world, max_over_ranks(v_ms, dev)), 4),
+                          "unit": UNIT, "steps": steps, "ms_per_step": round(v_ms / steps, 2), "status": int(vst),
+                          "outer_iters": vinfo.outer_iters, "gmres_iters": vinfo.gmres_iters_total,
+                          "final_rel_residual": vinfo.final_rel_residual}
+        if ref is not None and ref.shape == Hv.shape:
+            variants[name]["max_rel_diff_H_vs_headline"] = float(np.max(np.abs(Hv - ref)) / np.max(np.abs(ref)))
+
     v_steps = max(1, min(args.steps, 2))
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    v0.record(stream)
-    for _ in range(v_steps):
-        ctx.set_contrast_dev(s6_dev)
-        Hv, vinfo, vst = ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, vopts)
-    v1.record(stream)
-    torch.cuda.synchronize(dev)
-    v_ms = max_over_ranks(v0.elapsed_time(v1), dev)
-    variant = {"operator": other, "value": round(job_throughput(v_steps, world, v_ms), 4), "unit": UNIT,
-               "steps": v_steps, "ms_per_step": round(v_ms / v_steps, 2), "status": int(vst),
-               "outer_iters": vinfo.outer_iters, "gmres_iters": vinfo.gmres_iters_total,
-               "final_rel_residual": vinfo.final_rel_residual,
-               "max_rel_diff_H_vs_headline": float(np.max(np.abs(Hv - H)) / np.max(np.abs(H)))}
-    # ----------------------------------------------------------------- Krylov outer iteration variant
-    kopts = ie.make_opts(z_split=wl.z_split, restart=wl.restart, precision=ie.IE_PREC_MIXED, max_inner=4000,
-                         max_outer=60, contraction=contraction, outer_krylov=True, outer_restart=20,
-                         outer_inner_tol=0.1)
+    if bw.key == "c5":
+        variant("sequential_blocks", dict(bw.opts, concurrent_blocks=False), v_steps,
+                "the same solve with the block solves of each sweep one after another")
+        variant("device_graph_blocks", dict(bw.opts, graph=True), v_steps,
+                "the same solve with every block's GMRES as one CUDA graph, all launched before the first wait")
+        c2 = BenchWorkload("c2", rank_seed(args.seed, rank), args.scale, args.operator)
+        with ie.Context(c2.grid, c2.grid.h, c2.sigma0, c2.freq) as cctx:
+            cctx.set_stream(stream)
+            cctx.set_contrast(c2.sigma6)
+            variant("c2_gauss_seidel", c2.opts, max(1, min(args.steps, 3)), c2.description, ctx_=cctx,
+                    items=c2.items, dd=ie.IE_DD_GAUSS_SEIDEL, reupload=False)
+    else:
+        other = "conventional" if args.operator == "contraction" else "contraction"
+        variant(other, dict(bw.opts, contraction=(other == "contraction")), v_steps, f"{other} operator form")
+        variant("fgmres_outer", dict(bw.opts, outer_krylov=True, outer_restart=20, outer_inner_tol=0.1), v_steps,
+                "flexible GMRES(20) preconditioned by one GS sweep, block tol 0.1")
+    # ----------------------------------------------------------------- sub-domain operator bandwidth
+    z0, z1 = bw.block
+    nzb = z1 - z0
+    nb = 3 * nzb * g.ny * g.nx
     ctx.set_contrast_dev(s6_dev)
-    ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, kopts)
-    torch.cuda.synchronize(dev)
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    k0.record(stream)
-    for _ in range(v_steps):
-        ctx.set_contrast_dev(s6_dev)
-        Hk, kinfo, kst = ctx.solve(src, rx, ie.IE_DD_GAUSS_SEIDEL, wl.tol, kopts)
-    k1.record(stream)
-    torch.cuda.synchronize(dev)
-    k_ms = max_over_ranks(k0.elapsed_time(k1), dev)
-    kvariant = {"outer": "flexible GMRES(20) preconditioned by one GS sweep, block tol 0.1",
-                "operator": args.operator, "value": round(job_throughput(v_steps, world, k_ms), 4), "unit": UNIT,
-                "steps": v_steps, "ms_per_step": round(k_ms / v_steps, 2), "status": int(kst),
-                "outer_iters": kinfo.outer_iters, "gmres_iters": kinfo.gmres_iters_total,
-                "final_rel_residual": kinfo.final_rel_residual,
-                "max_rel_diff_H_vs_headline": float(np.max(np.abs(Hk - H)) / np.max(np.abs(H)))}
-    # ----------------------------------------------------------------- block operator bandwidth
-    nb = 3 * (g.nz // 2) * g.ny * g.nx
     x = torch.randn(nb, dtype=torch.complex64, device=dev)
     y = torch.empty_like(x)
     for _ in range(3):
-        ctx.matvec_dev(x, y, z0=0, nz=g.nz // 2)
+        ctx.matvec_dev(x, y, z0=z0, nz=nzb)
     torch.cuda.synchronize(dev)
     ctx.profile_enable(True)
     reps = 20
-    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    m0.record(stream)
-    for _ in range(reps):
-        ctx.matvec_dev(x, y, z0=0, nz=g.nz // 2)
-    m1.record(stream)
-    torch.cuda.synchronize(dev)
-    mv_ms = m0.elapsed_time(m1) / reps
+    mv_ms, _ = timed(stream, torch, dev, lambda k: ctx.matvec_dev(x, y, z0=z0, nz=nzb), reps, 1, dist)
+    mv_ms /= reps
     mprof = ctx.profile_read()
     ctx.profile_enable(False)
     mv_bytes = sum(mprof[k][2] for k in ("P1_c64", "P2_c64", "P3_c64", "P4_c64", "P5_c64")) / reps
-    n_block = (g.nz // 2) * g.ny * g.nx
+    n_block = nzb * g.ny * g.nx
     peak, peak_kind = measured_peaks()
     # ----------------------------------------------------------------- roofline of the dominant kernel
     dom = max(prof, key=lambda k: prof[k][1])
@@ -407,42 +457,57 @@ def run_gb300(args):
     last = infos[-1]
     # ----------------------------------------------------------------- CPU oracle baseline
     cpu_baseline = None
+    contraction = args.operator == "contraction"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_setup, t_apply = oracle_block_sample(wl, 0, g.nz // 2, n_apply=1, contraction=contraction)
-        # whole-grid applications (FP64 residual) cost about twice a sub-domain one (twice the volume)
-        applications = last.matvecs + 2 * (last.outer_iters + 1) + last.outer_iters
-        est = 3 * t_setup + t_apply * applications
-        cpu_baseline = {"value": 1.0 / est, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                        "sample": (f"CPU FP64 oracle: spectra of one 128^3 sub-domain ({t_setup:.1f} s) + one operator "
-                                   f"application ({t_apply:.1f} s), scaled to this solve's {applications} "
-                                   f"sub-domain-operator equivalents (GMRES applications + 2x per FP64 residual + "
-                                   f"interaction updates) and 3 spectra setups (an extrapolation; the directly timed "
-                                   f"full solve is timed_full_solve)"),
-                        "seconds_per_solve_estimate": est,
-                        "timed_full_solve": c1_full_solves(ie, torch, dev, stream)}
+        if bw.key == "c5":
+            nzs = max(1, nzb // 4)  # a quarter of a sub-domain: a bounded sample
+            t_setup, t_apply = oracle_block_sample(bw, nzs, 1, contraction)
+            unit_v = padded_volume(g, nzs)
+            blk = padded_volume(g, nzb) / unit_v
+            whole = padded_volume(g, g.nz) / unit_v
+            whole_apps = last.outer_iters + 2 + last.outer_iters // 20
+            est = t_setup * (blk + whole) + t_apply * (last.matvecs * blk + whole_apps * whole)
+            sample = (f"CPU FP64 oracle: spectra ({t_setup:.1f} s) and one operator application ({t_apply:.1f} s) of a "
+                      f"{g.nx}x{g.ny}x{nzs} slab of the model, scaled by padded FFT volume to this solve's "
+                      f"{last.matvecs} sub-domain applications ({blk:.0f}x the slab), {whole_apps} whole-grid "
+                      f"applications ({whole:.0f}x) and one spectra setup of each size: an extrapolation; "
+                      f"the directly timed full solve is timed_full_solve")
+        else:
+            t_setup, t_apply = oracle_block_sample(bw, nzb, 1, contraction)
+            applications = last.matvecs + 2 * (last.outer_iters + 1) + last.outer_iters
+            est = 3 * t_setup + t_apply * applications
+            sample = (f"CPU FP64 oracle: spectra of one {g.nx}x{g.ny}x{nzb} sub-domain ({t_setup:.1f} s) + one operator "
+                      f"application ({t_apply:.1f} s), scaled to this solve's {applications} sub-domain-operator "
+                      f"equivalents and 3 spectra setups: an extrapolation; the directly timed full solve is "
+                      f"timed_full_solve")
+        cpu_baseline = {"value": 1.0 / est, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample,
+                        "seconds_per_solve_estimate": est, "timed_full_solve": c1_full_solves(ie, torch, dev, stream)}
     out = {
-        "metric": METRIC, "value": (round(value, 4) if value is not None else None), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(t_ms_max / args.steps, 2), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic (seeded generator)",
-        "config": {"workload": WORKLOAD, "grid": [g.nx, g.ny, g.nz], "h_m": g.h, "sub_domains": wl.z_split,
-                   "dd": "block Gauss-Seidel, adaptive tol e/10", "precision": "complex64 conv/Krylov + FP64 refinement",
-                   "operator": args.operator,
-                   "restart": wl.restart, "tol": wl.tol, "freq_hz": wl.freq, "sigma0": wl.sigma0, "seed": args.seed,
+        "metric": METRIC, "value": (round(value, 4) if value is not None else None), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms_max / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": bw.description, "grid": [g.nx, g.ny, g.nz], "h_m": g.h, "sub_domains": bw.split,
+                   "dd": bw.dd_text, "precision": "complex64 conv/Krylov + FP64-accurate refinement",
+                   "operator": args.operator, "restart": bw.opts["restart"], "tol": bw.tol, "freq_hz": bw.freq,
+                   "sigma0": bw.sigma0, "seed": args.seed, "positions": len(bw.items),
                    "setup_s_excluded": round(setup_s, 3), "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": f"{world} independent tool positions (one per GPU)"},
-        "e2e": {"value": (round(e2e_value, 4) if e2e_value is not None else None), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                   "parallelism": f"{world} independent models (one per GPU)"},
+        "e2e": {"value": (round(e2e_value, 4) if e2e_value is not None else None), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d_total / args.steps), "d2h_bytes_per_step": int(d2h_total / args.steps)},
         "roofline": roofline,
-        "matvec": {"sub_domain": [g.nx, g.ny, g.nz // 2], "ms": round(mv_ms, 4),
-                   "algorithmic_GB": round(mv_bytes / 1e9, 4), "GBps": round(mv_bytes / 1e9 / (mv_ms / 1e3), 1),
+        "matvec": {"sub_domain": [g.nx, g.ny, nzb], "ms": round(mv_ms, 4), "algorithmic_GB": round(mv_bytes / 1e9, 4),
+                   "GBps": round(mv_bytes / 1e9 / (mv_ms / 1e3), 1),
                    "frac_of_peak": round(mv_bytes / 1e9 / (mv_ms / 1e3) / peak, 4),
                    "bytes_per_voxel": round(mv_bytes / n_block, 1)},
         "solve": {"status": int(st), "all_steps_converged": not failed, "failed_steps": failed,
-                  "profiled_pass": {"steps": prof_steps, "ms_per_step": round(prof_ms / prof_steps, 2)}, "outer_iters": last.outer_iters, "gmres_iters": last.gmres_iters_total,
-                  "matvecs": last.matvecs, "reorth_passes": last.reorth_passes,
-                  "final_rel_residual": last.final_rel_residual,
+                  "profiled_pass": {"steps": prof_steps, "ms_per_step": round(p_ms / prof_steps, 2)},
+                  "outer_iters": last.outer_iters, "gmres_iters": last.gmres_iters_total, "matvecs": last.matvecs,
+                  "reorth_passes": last.reorth_passes, "final_rel_residual": last.final_rel_residual,
+                  "ms_per_position": [round(1e3 * inf.seconds, 1) for inf in infos],
                   "residual_history": [float(v) for v in last.history()],
                   "H_rx_z": [[float(H[0, r, 2].real), float(H[0, r, 2].imag)] for r in range(H.shape[1])]},
-        "variants": {other: variant, "fgmres_outer": kvariant},
+        "variants": variants,
         "kernels": breakdown,
         "tuned_tiles": ie.tuned_tiles().strip().splitlines(),
         "gpu_launches": gpu_launches,
@@ -457,29 +522,39 @@ def run_gb300(args):
 
 
 # ------------------------------------------------------------------------------------ reference arm
+# Operator applications of one solve, as the GB300 arm counts them (sub-domain applications of GMRES,
+# whole-grid applications of the outer iteration and residuals), used only to scale the reference arm's
+# CPU sample to solves/s, because that arm runs without the GB300 one.
+REF_COUNTS = {("c5", "contraction"): (780, 18), ("c5", "conventional"): (1900, 18),
+              ("c2", "contraction"): (260, 11), ("c2", "conventional"): (650, 11)}
+
+
 def run_reference(args):
-    """The CPU FP64 oracle as the reference: each step times one bounded sample (one application of
-    the 128^3 sub-domain operator in the selected form) and converts it to solves/s with a fixed
-    operator-application count."""
+    """The CPU FP64 oracle as the reference arm: its spectra once, then each step times one bounded sample
+    (one application of the oracle's operator, in the selected form, on a slab of the workload's model:
+    a quarter of a 256x256x64 sub-domain for c5, a whole 128^3 sub-domain for c2), converted to solves/s
+    by padded FFT volume and the operator-application counts of one solve (REF_COUNTS): an extrapolation,
+    stated as such in the line."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from paper_2306_17537_gb300 import inputs
-
     import numpy as np
 
     from oracle import contraction as oc
     from oracle import operator as oop
 
-    wl = inputs.config2(args.seed, scale=args.scale)
-    nzb = wl.grid.nz // 2
+    bw = BenchWorkload(args.workload, args.seed, args.scale, args.operator)
+    g = bw.grid
+    nzb = bw.block[1] - bw.block[0]
+    nzs = max(1, nzb // 4) if bw.key == "c5" else nzb
+    s6 = bw.sigma6[:nzs]
     t0 = time.perf_counter()
     if args.operator == "contraction":
-        op = oc.ContractionOperator(wl.sigma6[:nzb], wl.grid.h, wl.freq, wl.sigma0)
+        op = oc.ContractionOperator(s6, g.h, bw.freq, bw.sigma0)
     else:
-        op = oop.FFTOperator(oop.contrast(wl.sigma6[:nzb], wl.sigma0), wl.grid.h, wl.freq, wl.sigma0)
+        op = oop.FFTOperator(oop.contrast(s6, bw.sigma0), g.h, bw.freq, bw.sigma0)
     t_setup = time.perf_counter() - t0
-    x = np.ones((3, nzb, wl.grid.ny, wl.grid.nx), dtype=np.complex128)
+    x = np.ones((3, nzs, g.ny, g.nx), dtype=np.complex128)
     for _ in range(min(args.warmup, 1)):
         op(x)
     times = []
@@ -488,16 +563,18 @@ def run_reference(args):
         op(x)
         times.append(time.perf_counter() - t0)
     t_apply = sum(times) / len(times)
-    n_block, n_full = REF_APPLICATIONS_PER_SOLVE[args.operator]
-    applications = n_block + 2 * n_full
-    est = 3 * t_setup + t_apply * applications
+    n_block, n_whole = REF_COUNTS[(bw.key, args.operator)]
+    unit_v = padded_volume(g, nzs)
+    blk, whole = padded_volume(g, nzb) / unit_v, padded_volume(g, g.nz) / unit_v
+    est = t_setup * (blk + whole) + t_apply * (n_block * blk + n_whole * whole)
     value = 1.0 / est
-    sample = (f"one application of the CPU FP64 oracle's 128^3 sub-domain operator per step (mean {t_apply:.2f} s) "
-              f"+ spectra setup ({t_setup:.1f} s), scaled to {applications} sub-domain-operator equivalents per solve")
+    sample = (f"one application of the CPU FP64 oracle's operator on a {g.nx}x{g.ny}x{nzs} slab per step (mean "
+              f"{t_apply:.2f} s; spectra {t_setup:.1f} s), scaled by padded FFT volume to {n_block} sub-domain and "
+              f"{n_whole} whole-grid applications and one spectra setup of each size per solve: an extrapolation")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(1e3 * t_apply, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded generator)",
-           "config": {"workload": WORKLOAD, "seed": args.seed, "operator": args.operator}, "impl": "reference",
+           "config": {"workload": bw.description, "seed": args.seed, "operator": args.operator}, "impl": "reference",
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

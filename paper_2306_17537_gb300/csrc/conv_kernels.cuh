@@ -250,7 +250,11 @@ __global__ void __launch_bounds__(P3Cfg<T, L, NT>::NTH, P3Cfg<T, L, NT>::MINB) k
     const bool nxy = xlo != ylo;
     const C<T>* gb = G + (long)iy * ox + ix;
     LaneSM<T, W> s0{spec(0) + w}, s1{spec(1) + w}, s2{spec(2) + w};
-    auto product = [&](int kz, int iz, bool nxz, bool nyz) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const bool zlo = (E == 1) || (m < E / 2);  // lower half of kz: s_z = +1
+      const int kz = t + TT * m, iz = zlo ? kz : L - kz;
+      const bool nxz = zlo ? !xlo : xlo, nyz = zlo ? !ylo : ylo;
       const C<T>* g = gb + iz * ozs;
       const C<T> gxx = ldgv(g), gyy = ldgv(g + ocs), gzz = ldgv(g + 2 * ocs);
       const C<T> gxy = ldgv(g + 3 * ocs), gxz = ldgv(g + 4 * ocs), gyz = ldgv(g + 5 * ocs);
@@ -258,17 +262,6 @@ __global__ void __launch_bounds__(P3Cfg<T, L, NT>::NTH, P3Cfg<T, L, NT>::MINB) k
       s0.st(kz, add_signed(add_signed(cmul(gxx, j0), nxy, cmul(gxy, j1)), nxz, cmul(gxz, j2)));
       s1.st(kz, add_signed(add_signed(cmul(gyy, j1), nxy, cmul(gxy, j0)), nyz, cmul(gyz, j2)));
       s2.st(kz, add_signed(add_signed(cmul(gzz, j2), nxz, cmul(gxz, j0)), nyz, cmul(gyz, j1)));
-    };
-    constexpr int half = E == 1 ? 1 : E / 2;
-#pragma unroll 4
-    for (int m = 0; m < half; ++m) {  // lower half of kz: s_z = +1
-      const int kz = t + TT * m;
-      product(kz, kz, !xlo, !ylo);
-    }
-#pragma unroll 4
-    for (int m = half; m < E; ++m) {  // upper half: s_z = -1
-      const int kz = t + TT * m;
-      product(kz, L - kz, xlo, ylo);
     }
   }
   // inverse z-FFT of each component and crop

@@ -1062,9 +1062,18 @@ ie_status build_gmres_graph(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>*
   return IE_OK;
 }
 
+template <typename T> struct GraphRun {  // one launched GMRES graph whose results are still on the device
+  GmGraph* G = nullptr;
+  long n = 0;
+  int m = 0;
+};
+
+// Launches GMRES as one CUDA graph on the context stream (see gmres_graph) without waiting for it:
+// gmres_graph_finish reads its outcome. Several contexts' graphs can so run at the same time with one
+// host synchronisation each at the end.
 template <typename T>
-ie_status gmres_graph(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, double tol, int m, int max_it,
-                      GmresOut* out) {
+ie_status gmres_graph_launch(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, double tol, int m, int max_it,
+                             GraphRun<T>* run) {
   const bool cgs2 = tol < kReorthTol;
   const long n = 3 * A.nb();
   CKS(ensure_scalars(c));
@@ -1074,7 +1083,6 @@ ie_status gmres_graph(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, do
   CK(c->kt1.ensure(sizeof(C<T>) * (size_t)n));
   CK(c->gm_state.ensure(sizeof(GmState)));
   for (int k = 0; k < 3; ++k) CKS(cap_stream(c, k));
-  *out = GmresOut();
   // outside any capture: allocates the block's workspaces and tunes its tiles
   C<T>* V = c->V.as<C<T>>();
   CKS(A.apply(V, V + ld));
@@ -1124,6 +1132,21 @@ ie_status gmres_graph(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, do
   CK(cudaMemcpyAsync(stage, st, hdr, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(stage + lens, reinterpret_cast<unsigned char*>(st) + offsetof(GmState, cyc_len),
                      sizeof(int) * kGmMaxCycles, cudaMemcpyDeviceToHost, s));
+  run->G = G;
+  run->n = n;
+  run->m = m;
+  return IE_OK;
+}
+
+// Waits for a graph started by gmres_graph_launch and collects its outcome and launch accounting.
+template <typename T> ie_status gmres_graph_finish(ie_ctx* c, const GraphRun<T>& run, GmresOut* out) {
+  GmGraph* G = run.G;
+  const long n = run.n;
+  const int m = run.m;
+  unsigned char* stage = reinterpret_cast<unsigned char*>(c->hpin);
+  const size_t hdr = offsetof(GmState, cs), lens = 256;
+  GmHead hs;
+  *out = GmresOut();
   CK(sync(c));
   std::memcpy(&hs, stage, hdr);
   std::vector<int> cyc(kGmMaxCycles);
@@ -1149,6 +1172,14 @@ ie_status gmres_graph(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, do
   out->rel = hs.rel;
   out->converged = hs.status == 1;
   return IE_OK;
+}
+
+template <typename T>
+ie_status gmres_graph(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, double tol, int m, int max_it,
+                      GmresOut* out) {
+  GraphRun<T> run;
+  CKS(gmres_graph_launch<T>(c, A, b, x, tol, m, max_it, &run));
+  return gmres_graph_finish<T>(c, run, out);
 }
 
 struct SolveCfg {
@@ -1494,8 +1525,32 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
     const ie_status ost = order_workers(c, ev);
     cudaEventDestroy(ev);  // released once the recorded work completes
     CKS(ost);
-    std::vector<std::thread> pool;
-    for (auto& job : jobs)
+    if (cfg.graph) {
+      // device-driven block solves: each block's GMRES graph is launched on its worker stream from this
+      // thread, all of them before the first wait, so the whole sweep runs on the GPU with one host
+      // synchronisation per block at its end
+      std::vector<GraphRun<T>> runs(jobs.size());
+      std::vector<BlockOp<T>> wops(jobs.size());
+      for (size_t k = 0; k < jobs.size(); ++k) {
+        ie_ctx* w = c->workers[jobs[k].i];
+        jobs[k].st = make_block<T>(w, 0, w->nz, &wops[k], cfg.contraction != 0);
+        if (jobs[k].st == IE_OK)
+          jobs[k].st = gmres_graph_launch<T>(w, wops[k], w->kb.template as<C<T>>(), w->kx.template as<C<T>>(),
+                                             jobs[k].tol, cfg.restart, cfg.max_inner, &runs[k]);
+      }
+      for (size_t k = 0; k < jobs.size(); ++k) {
+        ie_ctx* w = c->workers[jobs[k].i];
+        if (jobs[k].st == IE_OK) jobs[k].st = gmres_graph_finish<T>(w, runs[k], &jobs[k].go);
+        if (jobs[k].st == IE_OK) jobs[k].st = wops[k].to_field(w->kx.template as<C<T>>());
+      }
+      for (size_t k = 0; k < jobs.size(); ++k) {
+        ie_ctx* w = c->workers[jobs[k].i];
+        if (sync(w) != cudaSuccess && jobs[k].st == IE_OK) jobs[k].st = fail(w, IE_ECUDA, "sub-domain solve on its stream");
+      }
+    }
+    std::vector<std::thread> pool;  // host-driven block solves: one host thread per block
+    for (auto& job : jobs) {
+      if (cfg.graph) break;
       pool.emplace_back([&, jp = &job]() {
         cudaSetDevice(c->dev);
         ie_ctx* w = c->workers[jp->i];
@@ -1503,12 +1558,11 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
         jp->st = make_block<T>(w, 0, w->nz, &A, cfg.contraction != 0);
         C<T>* rhs_w = w->kb.template as<C<T>>();
         C<T>* dx_w = w->kx.template as<C<T>>();
-        if (jp->st == IE_OK)
-          jp->st = cfg.graph ? gmres_graph<T>(w, A, rhs_w, dx_w, jp->tol, cfg.restart, cfg.max_inner, &jp->go)
-                             : gmres<T>(w, A, rhs_w, dx_w, true, jp->tol, cfg.restart, cfg.max_inner, &jp->go);
+        if (jp->st == IE_OK) jp->st = gmres<T>(w, A, rhs_w, dx_w, true, jp->tol, cfg.restart, cfg.max_inner, &jp->go);
         if (jp->st == IE_OK) jp->st = A.to_field(dx_w);
         if (jp->st == IE_OK && sync(w) != cudaSuccess) jp->st = fail(w, IE_ECUDA, "sub-domain solve on its stream");
       });
+    }
     for (auto& t : pool) t.join();
     for (const auto& job : jobs)
       if (job.st != IE_OK) return fail(c, job.st, "sub-domain " + std::to_string(job.i) + ": " + c->workers[job.i]->err);
