@@ -1,15 +1,20 @@
 """Small, fixed invocations of single parts of the path, for kernel profiling and quick timing.
 
-    python -m paper_2306_17537_gb300.kernel_cases matvec   --n 128 [--fp64 | --dfloat] [--reps 5]
-        repeated sub-domain operator y = (I - G dsigma) x on an n^3 grid (five FFT passes), complex64
+    python -m paper_2306_17537_gb300.kernel_cases matvec   --n 128 [--shape nx,ny,nz] [--fp64 | --dfloat] [--reps 5]
+        repeated sub-domain operator y = (I - G dsigma) x on an n^3 (or nx x ny x nz) grid, complex64
         by default, complex128 or double-float (the outer-residual kernels) on request
     python -m paper_2306_17537_gb300.kernel_cases gmres    --scale 2 [--iters 60]
         one restarted GMRES(30) run on a sub-domain of the 128x128x256 workload divided by `scale`
     python -m paper_2306_17537_gb300.kernel_cases solve    --scale 2
         one complete forward solve (Algorithm 1) of the same workload
+    python -m paper_2306_17537_gb300.kernel_cases large    --scale 1 [--position 5]
+        one warm-up and one measured solve of the 256x256x512 benchmark model as bench.py solves it
+        (flexible GMRES over concurrent block-Jacobi sweeps); prints the measured solve's launch count, so
+        a launch list of the whole run can be cut to its last launches
     python -m paper_2306_17537_gb300.kernel_cases batch    --positions 8 [--scale 1] [--lanes 4]
         the batched logging workload: positions x {100 kHz, 2 MHz} tool-aligned windows, block Jacobi,
-        solved with ie_solve_batch (lanes contexts per frequency), then one at a time for comparison
+        solved with ie_solve_batch (lanes contexts per frequency), then one at a time for comparison;
+        contraction form; --conc runs each window's two sub-domain solves in flight together
 
 Each prints the elapsed device time and the per-kernel-class accounting of the library.
 """
@@ -35,23 +40,28 @@ def main(argv=None):
     from . import ie, inputs
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["matvec", "gmres", "solve", "batch"])
+    ap.add_argument("case", choices=["matvec", "gmres", "solve", "batch", "large"])
+    ap.add_argument("--position", type=int, default=5)
     ap.add_argument("--positions", type=int, default=8)
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--freqs", default="1e5,2e6", help="batch case: comma-separated frequencies")
     ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--shape", default=None, help="matvec case: nx,ny,nz instead of n^3")
     ap.add_argument("--scale", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--iters", type=int, default=60)
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--dfloat", action="store_true")
+    ap.add_argument("--conc", action="store_true", help="batch case: sub-domain solves of a sweep in flight together")
+    ap.add_argument("--graph", action="store_true", help="batch case: each block GMRES as one CUDA graph")
     a = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     out = {"case": a.case}
     if a.case == "matvec":
-        g = inputs.centred_grid(a.n, a.n, a.n, 0.25)
+        nx, ny, nz = [int(v) for v in a.shape.split(",")] if a.shape else (a.n, a.n, a.n)
+        g = inputs.centred_grid(nx, ny, nz, 0.25)
         s6 = inputs.dipping_ti_with_ellipsoids(g, 0)
         ctx = _ctx(g, 0.1, 4.0e5, s6)
         ctx.set_stream(stream)
@@ -101,7 +111,8 @@ def main(argv=None):
             count[w.freq] = k + 1
             batch.append(dict(ctx=ctxs[w.freq][k % a.lanes], sigma6=w.sigma6, sources=w.sources,
                               receivers=w.receivers, dd_mode=ie.IE_DD_JACOBI, tol=w.tol,
-                              opts=ie.make_opts(z_split=w.z_split, restart=w.restart, max_inner=4000, max_outer=60)))
+                              opts=ie.make_opts(z_split=w.z_split, restart=w.restart, max_inner=4000, max_outer=60,
+                                                contraction=True, concurrent_blocks=a.conc, graph=a.graph)))
         ie.solve_batch(batch[:2])  # warm-up: spectra of every sub-domain height, tile tuning
         for mode, conc in (("concurrent", 0), ("one at a time", 1)):
             t0 = time.perf_counter()
@@ -112,6 +123,19 @@ def main(argv=None):
                          "max_rel_residual": max(r[1].final_rel_residual for r in res),
                          "gmres_iters": [r[1].gmres_iters_total for r in res]}
         ctx = next(iter(ctxs.values()))[0]
+    elif a.case == "large":
+        wl = inputs.config5(0, a.position, scale=max(a.scale, 1))
+        ctx = _ctx(wl.grid, wl.sigma0, wl.freq, wl.sigma6)
+        ctx.set_stream(stream)
+        opts = ie.make_opts(z_split=wl.z_split, restart=wl.restart, max_inner=4000, max_outer=60, contraction=True,
+                            concurrent_blocks=True, outer_krylov=True, outer_restart=20, outer_inner_tol=0.1)
+        ctx.solve(wl.sources, wl.receivers, ie.IE_DD_JACOBI, wl.tol, opts)  # warm-up: spectra, workers, tiles
+        torch.cuda.synchronize()
+        ctx.profile_enable(True)
+        H, info, st = ctx.solve(wl.sources, wl.receivers, ie.IE_DD_JACOBI, wl.tol, opts)
+        out.update({"status": int(st), "sweeps": info.outer_iters, "gmres_iters": info.gmres_iters_total,
+                    "e": info.final_rel_residual, "seconds": info.seconds,
+                    "launches_measured": int(sum(v[0] for v in ctx.profile_read().values()))})
     else:
         wl = inputs.config2(0, scale=a.scale)
         ctx = _ctx(wl.grid, wl.sigma0, wl.freq, wl.sigma6)
