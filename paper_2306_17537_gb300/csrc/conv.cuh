@@ -8,7 +8,7 @@ namespace ie {
 enum Epilogue { EPI_APPLY = 0, EPI_ACCUM128 = 1, EPI_RESID128 = 2, EPI_CONV = 3 };
 
 bool supported_pencil(int L);
-constexpr int kTileVariants = 2;    // P2, P4
+constexpr int kTileVariants = 3;    // P2, P4
 constexpr int kP3TileVariants = 6;  // P3 (see ConvLaunch::p3)
 
 template <typename T> struct ConvLaunch {
@@ -19,7 +19,7 @@ template <typename T> struct ConvLaunch {
   static cudaError_t p5(int L, int mode, const C<T>* A, long A_cs, int nx, long nrows, const FieldC<T>* xin,
                         long x_cs, FieldC<T>* y, long y_cs, double2* r, long r_cs, const double2* b, long b_cs,
                         const C<T>* tw, cudaStream_t s);
-  // variant: 0 = default tile, 1 = half the lanes per block (choices for the autotuner)
+  // variant: tiles of about 256 (0), 128 (1) and 512 (2) threads (choices for the autotuner)
   static cudaError_t lanes(int L, int sign, int variant, const C<T>* in, long in_cs, long in_zs, long in_es,
                            int n_in, C<T>* out, long out_cs, long out_zs, long out_es, int n_out, int nlanes,
                            int nbatch, int ncomp, const C<T>* tw, cudaStream_t s);

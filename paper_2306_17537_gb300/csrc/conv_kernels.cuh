@@ -23,12 +23,15 @@ template <typename T, int L> struct RowCfg {  // pencils contiguous in memory (x
   static constexpr int P0 = kThreads / TT;
   static constexpr int P = P0 < 1 ? 1 : (P0 > 64 ? 64 : P0);  // pencils per block
 };
-// Pencils strided, W neighbouring pencils (lanes) per block. WDIV = 2 is the narrower tile the
-// autotuner may pick (half the lanes, half the threads per block).
-template <typename T, int L, int WDIV = 1> struct LaneCfg {
+// Pencils strided, W neighbouring pencils (lanes) per block, W = NT / TT for about NT threads: the
+// default tile of 256 threads, a narrower one of 128 and a wider one of 512 (longer contiguous row
+// segments) are the autotuner's choices.
+template <typename T, int L, int NT = kThreads> struct LaneCfg {
   static constexpr int TT = Plan<T, L>::TT;
-  static constexpr int W0 = kThreads / TT / WDIV;
+  static constexpr int W0 = NT / TT;
   static constexpr int W = W0 < 1 ? 1 : (W0 > 32 ? 32 : W0);
+  static constexpr int NTH = W * TT;
+  static constexpr size_t kSmem = (size_t)L * W * sizeof(C<T>);
 };
 
 // ---------------------------------------------------------------- P1: J = dsigma x, x-FFT
@@ -117,13 +120,14 @@ __global__ void __launch_bounds__(kThreads) k_p5_ifftx_epilogue(
 
 // ---------------------------------------------------------------- strided FFT (P2, P4, setup)
 // Pencil element e of lane `lane`, batch z, component c sits at c*cs + z*zs + e*es + lane.
-template <typename T, int L, int SIGN, int WDIV>
-__global__ void __launch_bounds__(kThreads) k_lanes_fft(
+template <typename T, int L, int SIGN, int NT>
+__global__ void __launch_bounds__(LaneCfg<T, L, NT>::NTH) k_lanes_fft(
     const C<T>* __restrict__ in, long in_cs, long in_zs, long in_es, int n_in,
     C<T>* __restrict__ out, long out_cs, long out_zs, long out_es, int n_out, int nlanes,
     const C<T>* __restrict__ tw) {
-  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = LaneCfg<T, L, WDIV>::W;
-  __shared__ C<T> smem[L * W];
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = LaneCfg<T, L, NT>::W;
+  extern __shared__ __align__(16) unsigned char lanes_dyn[];
+  C<T>* smem = reinterpret_cast<C<T>*>(lanes_dyn);
   const int w = threadIdx.x, t = threadIdx.y;
   const long z = blockIdx.y, c = blockIdx.z;
   const int lane = blockIdx.x * W + w;

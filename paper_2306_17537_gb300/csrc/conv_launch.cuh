@@ -97,18 +97,29 @@ cudaError_t ConvLaunch<T>::p5(int L, int mode, const C<T>* A, long A_cs, int nx,
   return cudaGetLastError();
 }
 
-template <typename T, int N, int WDIV>
+template <typename T, int N, int NT>
 static cudaError_t lanes_launch(int sign, const C<T>* in, long in_cs, long in_zs, long in_es, int n_in, C<T>* out,
                                 long out_cs, long out_zs, long out_es, int n_out, int nlanes, int nbatch, int ncomp,
                                 const C<T>* tw, cudaStream_t s) {
-  constexpr int W = LaneCfg<T, N, WDIV>::W;
+  using Cfg = LaneCfg<T, N, NT>;
+  constexpr int W = Cfg::W;
+  static std::once_flag attr;
+  static cudaError_t ae = cudaSuccess;
+  std::call_once(attr, [] {
+    if (Cfg::kSmem > 48 * 1024) {
+      ae = cudaFuncSetAttribute(k_lanes_fft<T, N, -1, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+      if (ae == cudaSuccess)
+        ae = cudaFuncSetAttribute(k_lanes_fft<T, N, 1, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    }
+  });
+  if (ae != cudaSuccess) return ae;
   dim3 blk(W, Plan<T, N>::TT), grd((unsigned)((nlanes + W - 1) / W), (unsigned)nbatch, (unsigned)ncomp);
   if (sign < 0)
-    k_lanes_fft<T, N, -1, WDIV><<<grd, blk, 0, s>>>(in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out,
-                                                     nlanes, tw);
+    k_lanes_fft<T, N, -1, NT><<<grd, blk, Cfg::kSmem, s>>>(in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es,
+                                                            n_out, nlanes, tw);
   else
-    k_lanes_fft<T, N, 1, WDIV><<<grd, blk, 0, s>>>(in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out,
-                                                    nlanes, tw);
+    k_lanes_fft<T, N, 1, NT><<<grd, blk, Cfg::kSmem, s>>>(in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es,
+                                                           n_out, nlanes, tw);
   return cudaGetLastError();
 }
 
@@ -118,12 +129,16 @@ cudaError_t ConvLaunch<T>::lanes(int L, int sign, int variant, const C<T>* in, l
                                  int nbatch, int ncomp, const C<T>* tw, cudaStream_t s) {
   if (nbatch <= 0 || nlanes <= 0 || ncomp <= 0) return cudaSuccess;
   switch (L) {
-#define IE_CASE(N)                                                                                                 \
-  case N:                                                                                                          \
-    return variant ? lanes_launch<T, N, 2>(sign, in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out, \
-                                           nlanes, nbatch, ncomp, tw, s)                                          \
-                   : lanes_launch<T, N, 1>(sign, in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out, \
-                                           nlanes, nbatch, ncomp, tw, s);
+#define IE_CASE(N)                                                                                                  \
+  case N:                                                                                                           \
+    switch (variant) {                                                                                              \
+      case 1: return lanes_launch<T, N, 128>(sign, in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out, \
+                                             nlanes, nbatch, ncomp, tw, s);                                          \
+      case 2: return lanes_launch<T, N, 512>(sign, in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out, \
+                                             nlanes, nbatch, ncomp, tw, s);                                          \
+      default: return lanes_launch<T, N, 256>(sign, in, in_cs, in_zs, in_es, n_in, out, out_cs, out_zs, out_es, n_out,\
+                                              nlanes, nbatch, ncomp, tw, s);                                         \
+    }
     IE_FOR_EACH_L(IE_CASE)
 #undef IE_CASE
     default:

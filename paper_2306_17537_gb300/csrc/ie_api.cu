@@ -136,8 +136,8 @@ struct ie_ctx {
   DevBuf E, E0, R;  // c128 whole-grid fields
   DevBuf Ec64;      // complex64 copy of E for the early, complex64 residuals
   DevBuf AEb;       // complex64 A_ii E_i of every block (block right-hand-side norms; see solve_one)
-  DevBuf FV, FZ, PR;  // outer flexible GMRES: Arnoldi basis, preconditioned vectors, sweep residual
-  DevBuf FW32;        // its complex64 operator output
+  DevBuf FV, FZ, PR, PZ;  // outer flexible GMRES: Arnoldi basis, preconditioned vectors, sweep input/output
+  DevBuf FW32;            // its complex64 combination Z y
   bool has_field = false;
   DevBuf Einit;           // initial guess for the next solve (ie_set_initial_field_dev)
   bool has_init = false;
@@ -372,9 +372,9 @@ template <typename T> ie_status ensure_conv_ws(ie_ctx* c, int zcap) {
 }
 
 // ------------------------------------------------------------------ FFT tile autotuner
-// The strided passes (P2, P3, P4) have two tile shapes: the default and one with half the pencils per
-// block; P3 has a third with twice the pencils, and each of its three also with TMA staging of its input
-// pencils (six variants). The first convolution
+// The strided passes (P2, P3, P4) have three tile shapes: the default, one with half the pencils per
+// block and one with twice as many; P3 has each also with TMA staging of its input pencils (six
+// variants). The first convolution
 // of a new shape times every variant on the live buffers
 // (three timed launches each after a warm-up; the work is data independent) and keeps the fastest for
 // the rest of the process. Variants produce bit-identical results.
@@ -1193,38 +1193,63 @@ struct SolveCfg {
 
 // Flexible GMRES on the whole-grid system (I - G dsigma) E = E0 (eq. 8) over the active sub-domains,
 // right-preconditioned by one sweep of Algorithm 1 started from zero (Krylov outer iteration in place of
-// the fixed-point sweeps, as the paper's conclusion proposes). The Arnoldi vectors are whole-grid
-// complex128 fields with the slabs of inactive sub-domains zeroed; the operator is applied with the
-// complex64 convolution in mixed precision (the FP64-accurate double-float one in FP64 mode), and the
-// true residual that starts every cycle and decides convergence is FP64-accurate; classical Gram-Schmidt
-// with the DGKS second pass and FP64 Givens rotations on the host. Each outer step costs one sweep, one whole-grid application and the
-// orthogonalisation; the true residual is recomputed at every restart.
-template <typename T, class Sweep>
+// the fixed-point sweeps, as the paper's conclusion proposes). The Arnoldi and preconditioned vectors are
+// whole-grid fields with the slabs of inactive sub-domains zeroed, stored in VT: complex64 in mixed
+// precision, with the operator applied by the complex64 convolution (its rounding, ~1e-7 of |z|, stays
+// below the target), complex128 with the FP64-accurate double-float convolution in FP64 mode. In both
+// the field E is complex128 and the true residual that starts every cycle and decides convergence is
+// FP64-accurate. Classical Gram-Schmidt with the DGKS second pass and FP64 Givens rotations on the host.
+// Each outer step costs one sweep, one whole-grid application and the orthogonalisation.
+template <typename T, typename VT, class Sweep>
 ie_status fgmres_outer(ie_ctx* c, const SolveCfg& cfg, const std::vector<char>& act, Sweep& sweep, double e0norm,
                        double* e, int* sweeps, ie_info* info, bool record, bool fast_ok) {
+  constexpr bool f32 = std::is_same<VT, float>::value;
+  using CV = C<VT>;
   const long N3 = 3 * c->N, nxy = (long)c->nx * c->ny;
+  const long ld = (N3 + 1) & ~1L;  // even stride keeps every vector 16-byte aligned
   const int m = cfg.outer_restart;
   if (m < 1 || m > 127) return fail(c, IE_EINVAL, "outer restart must be in [1, 127]");
   cudaStream_t s = c->stream;
   CKS(ensure_scalars(c));
   SpecSet* S = nullptr;
   CKS(get_spec(c, c->nz, &S));
-  CK(c->FV.ensure(sizeof(double2) * (size_t)(m + 1) * N3));
-  CK(c->FZ.ensure(sizeof(double2) * (size_t)m * N3));
+  CK(c->FV.ensure(sizeof(CV) * (size_t)(m + 1) * ld));
+  CK(c->FZ.ensure(sizeof(CV) * (size_t)m * ld));
   CK(c->PR.ensure(sizeof(double2) * N3));
-  double2* V = c->FV.as<double2>();
-  double2* Z = c->FZ.as<double2>();
+  CK(c->PZ.ensure(sizeof(double2) * N3));
+  CV* V = c->FV.as<CV>();
+  CV* Z = c->FZ.as<CV>();
   double2* PR = c->PR.as<double2>();
+  double2* PZ = c->PZ.as<double2>();
   const RedScratch sc = scratch(c);
   double2* dh = c->dh.as<double2>();
   double2* dh2 = c->dh2.as<double2>();
   double2* dn = c->dnrm.as<double2>();
   int* flag = c->flag.as<int>();
-  auto mask = [&](double2* v) -> ie_status {  // zero the slabs of the sub-domains left out
+  const double vb = sizeof(CV);
+  auto mask = [&](auto* v) -> ie_status {  // zero the slabs of the sub-domains left out
+    using E = std::remove_pointer_t<decltype(v)>;
     for (size_t i = 0; i + 1 < cfg.split.size(); ++i) {
       if (act[i]) continue;
       const long off = (long)cfg.split[i] * nxy, nb = (long)(cfg.split[i + 1] - cfg.split[i]) * nxy;
-      for (int k = 0; k < 3; ++k) CK(cudaMemsetAsync(v + k * c->N + off, 0, sizeof(double2) * nb, s));
+      for (int k = 0; k < 3; ++k) CK(cudaMemsetAsync(v + k * c->N + off, 0, sizeof(E) * nb, s));
+    }
+    return IE_OK;
+  };
+  // c128 field -> VT vector and back (plain copies in FP64 mode)
+  auto to_vec = [&](const double2* src, CV* dst) -> ie_status {
+    if constexpr (f32)
+      KL(IE_K_FIELD, 24.0 * N3, launch_c128_to_c64(src, c->N, reinterpret_cast<float2*>(dst), c->N, c->N, s));
+    else
+      CK(cudaMemcpyAsync(dst, src, sizeof(double2) * N3, cudaMemcpyDeviceToDevice, s));
+    return IE_OK;
+  };
+  auto to_field = [&](const CV* src, double2* dst) -> ie_status {  // dst := src
+    if constexpr (f32) {
+      CK(cudaMemsetAsync(dst, 0, sizeof(double2) * N3, s));
+      KL(IE_K_FIELD, 40.0 * N3, launch_add_c64_to_c128(reinterpret_cast<const float2*>(src), c->N, dst, c->N, c->N, s));
+    } else {
+      CK(cudaMemcpyAsync(dst, src, sizeof(double2) * N3, cudaMemcpyDeviceToDevice, s));
     }
     return IE_OK;
   };
@@ -1233,44 +1258,35 @@ ie_status fgmres_outer(ie_ctx* c, const SolveCfg& cfg, const std::vector<char>& 
   while (*e > cfg.tol && *sweeps < cfg.max_outer) {
     CKS(mask(c->R.as<double2>()));
     const double beta = *e * e0norm;  // |R| over the active slabs
-    KL(IE_K_KRYLOV_MISC, 32.0 * N3, Krylov<double>::scale(c->R.as<double2>(), V, N3, nullptr, 1.0 / beta, s));
+    CKS(to_vec(c->R.as<double2>(), V));
+    KL(IE_K_KRYLOV_MISC, 2.0 * vb * N3, Krylov<VT>::scale(V, V, N3, nullptr, 1.0 / beta, s));
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jd = 0;
     for (int j = 0; j < m && *sweeps < cfg.max_outer; ++j) {
-      double2* vj = V + (size_t)j * N3;
-      double2* zj = Z + (size_t)j * N3;
-      double2* w = V + (size_t)(j + 1) * N3;
-      CK(cudaMemcpyAsync(PR, vj, sizeof(double2) * N3, cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemsetAsync(zj, 0, sizeof(double2) * N3, s));
+      CV* vj = V + (size_t)j * ld;
+      CV* zj = Z + (size_t)j * ld;
+      CV* w = V + (size_t)(j + 1) * ld;
+      CKS(to_field(vj, PR));
+      CK(cudaMemsetAsync(PZ, 0, sizeof(double2) * N3, s));
       int its = 0;
-      CKS(sweep(PR, zj, cfg.outer_inner_tol, &its));
+      CKS(sweep(PR, PZ, cfg.outer_inner_tol, &its));
       ++*sweeps;
-      if (fast_ok) {  // complex64 operator inside the Arnoldi process (mixed precision): its rounding,
-        // ~1e-7 of |z|, stays below the target, and every restart's true residual is FP64-accurate
-        CK(c->Ec64.ensure(sizeof(float2) * N3));
-        CK(c->FW32.ensure(sizeof(float2) * N3));
-        float2* z32 = c->Ec64.as<float2>();
-        float2* w32 = c->FW32.as<float2>();
-        KL(IE_K_FIELD, 24.0 * N3, launch_c128_to_c64(zj, c->N, z32, c->N, c->N, s));
-        CKS(conv<float>(c, S, z32, c->N, 0, c->nz, 0, c->nz, 0, EPI_APPLY, z32, c->N, w32, c->N, nullptr, 0, nullptr,
-                        0));
-        CK(cudaMemsetAsync(w, 0, sizeof(double2) * N3, s));
-        KL(IE_K_FIELD, 40.0 * N3, launch_add_c64_to_c128(w32, c->N, w, c->N, c->N, s));
-      } else {
+      CKS(to_vec(PZ, zj));
+      if constexpr (f32)
+        CKS(conv<float>(c, S, zj, c->N, 0, c->nz, 0, c->nz, 0, EPI_APPLY, zj, c->N, w, c->N, nullptr, 0, nullptr, 0));
+      else
         CKS(conv<df>(c, S, zj, c->N, 0, c->nz, 0, c->nz, 0, EPI_APPLY, zj, c->N, w, c->N, nullptr, 0, nullptr, 0));
-      }
       CKS(mask(w));
       const int nv = j + 1;
       const double ng = (nv + kDotGroup - 1) / kDotGroup;
-      KL(IE_K_DOTS, 16.0 * N3 * (nv + ng),
-         Krylov<double>::dots(V, N3, nv, w, N3, true, dh, nullptr, nullptr, sc, s));
-      KL(IE_K_UPDATE, 16.0 * N3 * (nv + 2),
-         Krylov<double>::update(V, N3, nv, dh, w, N3, dn, dh + nv, 0.5, flag, nullptr, sc, s));
-      KL(IE_K_DOTS, 0, Krylov<double>::dots(V, N3, nv, w, N3, false, dh2, dh, flag, sc, s));
-      KL(IE_K_UPDATE, 0, Krylov<double>::update(V, N3, nv, dh2, w, N3, dn, nullptr, 0.0, nullptr, flag, sc, s));
-      KL(IE_K_KRYLOV_MISC, 32.0 * N3, Krylov<double>::scale(w, w, N3, dn, 0.0, s));
+      KL(IE_K_DOTS, vb * N3 * (nv + ng), Krylov<VT>::dots(V, ld, nv, w, N3, true, dh, nullptr, nullptr, sc, s));
+      KL(IE_K_UPDATE, vb * N3 * (nv + 2),
+         Krylov<VT>::update(V, ld, nv, dh, w, N3, dn, dh + nv, 0.5, flag, nullptr, sc, s));
+      KL(IE_K_DOTS, 0, Krylov<VT>::dots(V, ld, nv, w, N3, false, dh2, dh, flag, sc, s));
+      KL(IE_K_UPDATE, 0, Krylov<VT>::update(V, ld, nv, dh2, w, N3, dn, nullptr, 0.0, nullptr, flag, sc, s));
+      KL(IE_K_KRYLOV_MISC, 2.0 * vb * N3, Krylov<VT>::scale(w, w, N3, dn, 0.0, s));
       CK(cudaMemcpyAsync(c->hpin, dh, sizeof(double2) * nv, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(c->hpin + nv, dn, sizeof(double2), cudaMemcpyDeviceToHost, s));
       CK(sync(c));
@@ -1306,8 +1322,16 @@ ie_status fgmres_outer(ie_ctx* c, const SolveCfg& cfg, const std::vector<char>& 
     }
     for (int i = 0; i < jd; ++i) c->hpin[i] = make_double2(y[i].real(), y[i].imag());
     CK(cudaMemcpyAsync(c->dy.as<double2>(), c->hpin, sizeof(double2) * jd, cudaMemcpyHostToDevice, s));
-    KL(IE_K_KRYLOV_MISC, 16.0 * N3 * (jd + 2),
-       Krylov<double>::combine(Z, N3, jd, c->dy.as<double2>(), c->E.as<double2>(), N3, s));
+    if constexpr (f32) {  // E += Z y: the combination in complex64, added to the complex128 field
+      CK(c->FW32.ensure(sizeof(float2) * N3));
+      float2* zy = c->FW32.as<float2>();
+      CK(cudaMemsetAsync(zy, 0, sizeof(float2) * N3, s));
+      KL(IE_K_KRYLOV_MISC, vb * N3 * (jd + 2), Krylov<float>::combine(Z, ld, jd, c->dy.as<double2>(), zy, N3, s));
+      KL(IE_K_FIELD, 40.0 * N3, launch_add_c64_to_c128(zy, c->N, c->E.as<double2>(), c->N, c->N, s));
+    } else {
+      KL(IE_K_KRYLOV_MISC, vb * N3 * (jd + 2),
+         Krylov<double>::combine(Z, ld, jd, c->dy.as<double2>(), c->E.as<double2>(), N3, s));
+    }
     CKS(full_residual(c, e0norm, e, fast_ok && *e > fast_residual_above(cfg.tol), fast_residual_above(cfg.tol)));
   }
   return IE_OK;
@@ -1607,7 +1631,10 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
   };
   int sweeps = 0;
   if (cfg.outer_krylov && cfg.dd_mode != IE_DD_NONE) {
-    CKS(fgmres_outer<T>(c, cfg, blk_active, sweep_any, e0norm, &e, &sweeps, info, record, fast_ok));
+    const ie_status ost =
+        fast_ok ? fgmres_outer<T, float>(c, cfg, blk_active, sweep_any, e0norm, &e, &sweeps, info, record, fast_ok)
+                : fgmres_outer<T, double>(c, cfg, blk_active, sweep_any, e0norm, &e, &sweeps, info, record, fast_ok);
+    CKS(ost);
   } else {
     while (e > cfg.tol && sweeps < cfg.max_outer) {
       int sweep_its = 0;
