@@ -222,6 +222,8 @@ cudaError_t ConvLaunch<T>::p3(int L, int variant, const C<T>* Bin, long in_cs, i
       case 3: return p3_launch<T, N, 64, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);   \
       case 4: return p3_launch<T, N, 256, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
       case 5: return p3_launch<T, N, 256, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
+      case 6: return p3_launch<T, N, 512, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
+      case 7: return p3_launch<T, N, 512, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
       default: return p3_launch<T, N, 128, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);\
     }
     IE_FOR_EACH_L(IE_CASE)

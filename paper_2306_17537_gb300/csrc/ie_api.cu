@@ -373,8 +373,8 @@ template <typename T> ie_status ensure_conv_ws(ie_ctx* c, int zcap) {
 
 // ------------------------------------------------------------------ FFT tile autotuner
 // The strided passes (P2, P3, P4) have three tile shapes: the default, one with half the pencils per
-// block and one with twice as many; P3 has each also with TMA staging of its input pencils (six
-// variants). The first convolution
+// block and one with twice as many (P3 a fourth with four times as many); P3 has each also with TMA
+// staging of its input pencils (eight variants). The first convolution
 // of a new shape times every variant on the live buffers
 // (three timed launches each after a warm-up; the work is data independent) and keeps the fastest for
 // the rest of the process. Variants produce bit-identical results.
