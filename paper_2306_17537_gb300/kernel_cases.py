@@ -128,7 +128,7 @@ def main(argv=None):
         ctx = _ctx(wl.grid, wl.sigma0, wl.freq, wl.sigma6)
         ctx.set_stream(stream)
         opts = ie.make_opts(z_split=wl.z_split, restart=wl.restart, max_inner=4000, max_outer=60, contraction=True,
-                            concurrent_blocks=True, outer_krylov=True, outer_restart=20, outer_inner_tol=0.1)
+                            concurrent_blocks=True, outer_krylov=True, outer_restart=20, outer_inner_tol=0.3)
         ctx.solve(wl.sources, wl.receivers, ie.IE_DD_JACOBI, wl.tol, opts)  # warm-up: spectra, workers, tiles
         torch.cuda.synchronize()
         ctx.profile_enable(True)
