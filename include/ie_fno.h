@@ -58,6 +58,14 @@ int64_t ie_fno_param_count(const ie_fno* fno);
 /* Issue all work on this CUDA stream (a cudaStream_t passed as void*; NULL = legacy default). */
 ie_status ie_fno_set_stream(ie_fno* fno, void* stream);
 
+/* Pointwise channel maps of the forward pass (the layers' v W + w, the head's Q1 and Q2) on the
+ * fifth-generation tensor cores (on = 1, the default) or on the CUDA cores (0). The tensor-core path is
+ * taken for BF16 storage when the map's input width is a multiple of 16 (at most 128) and its output
+ * width at most 128: BF16 operands, FP32 accumulation in tensor memory (tcgen05.mma); its results agree
+ * with the CUDA-core path to BF16 rounding. A kernel whose bounded wait for its MMAs gives up makes the
+ * next forward call return IE_ECUDA. IE_EINVAL for another value of on. */
+ie_status ie_fno_set_tensor_cores(ie_fno* fno, int32_t on);
+
 /* Load (and reset the Adam state) / read back the parameter vector, host FP32, synchronous. */
 ie_status ie_fno_set_params(ie_fno* fno, const float* host);
 ie_status ie_fno_get_params(ie_fno* fno, float* host);

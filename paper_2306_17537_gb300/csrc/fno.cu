@@ -13,13 +13,16 @@
 // Q1, q1, Q2, q2 — the order and layouts of the CPU reference.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "common.cuh"
 #include "ie_fno.h"
+#include "tcgen05.cuh"
 
 namespace ie {
 namespace fnok {
@@ -179,6 +182,117 @@ __global__ void k_mm_fwd(const SX* __restrict__ X, int I, const float* __restric
     if (Yf) Yf[idx] = acc;
   }
 }
+// The same map on the tensor cores, for BF16 X with I a multiple of 16 (16 <= I <= 128) and O <= 128:
+// tcgen05 MMAs of kind::f16 (BF16 operands, FP32 accumulation in tensor memory), M = 128 rows per tile,
+// N = O rounded up to 16, K = 16 per instruction. A persistent block of 128 threads keeps Mt (BF16,
+// transposed to O x I, K-major) in shared memory; per tile of 128 rows it loads X (GELU applied when
+// xgelu), one thread issues the I/16 MMAs and commits them to an mbarrier, every thread waits for it
+// (bounded: a timeout sets *err, waits once more and ends the loop; the block always frees its tensor
+// memory), then thread r reads row r of the product from tensor memory and writes the epilogue.
+constexpr int kTcRows = 128;
+
+template <typename SY>
+__global__ void __launch_bounds__(kTcRows) k_mm_fwd_tc(const __nv_bfloat16* __restrict__ X, int I,
+                                                     const float* __restrict__ Mt, const float* __restrict__ bias,
+                                                     const float* __restrict__ add, SY* __restrict__ Ypre,
+                                                     SY* __restrict__ Yact, float* __restrict__ Yf, int O, int Npad,
+                                                     unsigned ncols, long rows, int xgelu, int ygelu,
+                                                     int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tc_dyn[];
+  unsigned char* As = tc_dyn;                                // kTcRows x I BF16, K-major core matrices
+  unsigned char* Bs = tc_dyn + (size_t)kTcRows * I * 2;      // Npad x I BF16
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + (size_t)Npad * I * 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncwarp();  // the warp-wide (aligned) allocation below runs converged
+  if (warp == 0) {
+    tmem_alloc(tslot, ncols);
+    tmem_relinquish();
+  }
+  for (int q = tid; q < Npad * I; q += kTcRows) {  // B = Mt^T in BF16, rows o >= O zero
+    const int o = q / I, i = q % I;
+    const float v = o < O ? Mt[i * O + o] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(Bs + kmajor_offset(o, i, I)) = __float2bfloat16(v);
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = idesc_bf16_f32(kTcRows, Npad);
+  const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs), sbo = (uint32_t)(I >> 3) << 7;
+  const long ntiles = (rows + kTcRows - 1) / kTcRows;
+  const int cpr = I >> 3;  // 16-byte chunks (8 BF16) per row
+  unsigned phase = 0;
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long r0 = tile * kTcRows;
+    for (int q = tid; q < kTcRows * cpr; q += kTcRows) {
+      const int m = q / cpr, kc = q % cpr;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (r0 + m < rows) {
+        v = *reinterpret_cast<const uint4*>(X + (r0 + m) * I + kc * 8);
+        if (xgelu) {
+          __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float2 fv = __bfloat1622float2(h[j]);
+            fv.x = gelu(fv.x);
+            fv.y = gelu(fv.y);
+            h[j] = __float22bfloat162_rn(fv);
+          }
+        }
+      }
+      *reinterpret_cast<uint4*>(As + kmajor_offset(m, kc * 8, I)) = v;
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int s = 0; s < I / 16; ++s)
+        tc_mma_bf16(tmem, smem_desc(a0 + s * 256, 128, sbo), smem_desc(b0 + s * 256, 128, sbo), idesc, s > 0);
+      tc_commit(bar);
+    }
+    if (!__syncthreads_and(mbar_wait(bar, phase))) {
+      if (tid == 0) atomicExch(err, 1);
+      mbar_wait(bar, phase);  // once more, bounded, before the tensor memory is freed
+      break;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    const long r = r0 + tid;  // warp w owns tensor-memory lanes (rows) 32w .. 32w + 31
+    for (int c0 = 0; c0 < Npad; c0 += 16) {
+      float d[16];
+      __syncwarp();  // the warp-wide (aligned) load runs converged
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, d);
+      if (r < rows) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int o = c0 + j;
+          if (o < O) {
+            const long idx = r * O + o;
+            float acc = d[j] + bias[o];
+            if (add) acc += add[idx];
+            if (Ypre) stf(Ypre + idx, acc);
+            if (Yact) stf(Yact + idx, ygelu ? gelu(acc) : acc);
+            if (Yf) Yf[idx] = acc;
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // every read of this tile's product precedes the next tile's MMAs
+  }
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
 // dX[r][i] = (sum_o dY[r][o] Mt[i][o] + add[r][i]) * (zgelu ? gelu'(Z[r][i]) : 1)
 template <typename SZ>
 __global__ void k_mm_bwd_x(const float* __restrict__ dY, int O, const float* __restrict__ Mt,
@@ -386,12 +500,16 @@ struct ie_fno {
   float2 *V1 = nullptr, *V2 = nullptr, *V3 = nullptr, *Wm = nullptr;  // spectral intermediates (V3 per layer)
   float *kbuf = nullptr, *dv = nullptr, *dpre = nullptr, *dh = nullptr, *u = nullptr, *du = nullptr, *sums = nullptr;
   int adam_t = 0;
+  int tensor_cores = 1;    // BF16 pointwise maps on the tcgen05 path (ie_fno_set_tensor_cores)
+  int* tc_err = nullptr;   // mapped pinned flag: a tensor-core kernel's bounded wait gave up
+  int nsm = 0;
   cudaStream_t stream = nullptr;
   std::string err;
   ~ie_fno() {
     void* ptrs[] = {params, grads, m1, m2, Rs, v, pre, hp, V1, V2, V3, Wm, kbuf, dv, dpre, dh, u, du, sums};
     for (void* p : ptrs)
       if (p) cudaFree(p);
+    if (tc_err) cudaFreeHost(tc_err);
   }
   size_t ssz() const { return storage ? 2 : 4; }
   long rows(int B) const { return (long)B * Np; }
@@ -475,8 +593,43 @@ template <typename S> S* act(ie_fno* f, void* base_ptr, int l, int B, int ch) {
   return reinterpret_cast<S*>(base_ptr) + (long)l * f->rows(f->Bmax) * ch;
 }
 
+// Y = f(X) Mt + bias (+ add) on the tensor cores when the network stores BF16 activations and the shape
+// allows it (I a multiple of 16 up to 128, O up to 128); otherwise, or with tensor cores switched off,
+// on the CUDA cores (k_mm_fwd).
+template <typename SX, typename SY>
+cudaError_t mm_fwd(ie_fno* f, const SX* X, int I, const float* Mt, const float* bias, const float* add, SY* Ypre,
+                   SY* Yact, float* Yf, int O, long rows, int xgelu, int ygelu) {
+  if constexpr (std::is_same<SX, __nv_bfloat16>::value) {
+    if (f->tensor_cores && I % 16 == 0 && I >= 16 && I <= 128 && O <= 128 && rows > 0) {
+      const int Npad = (O + 15) / 16 * 16;
+      unsigned ncols = 32;
+      while ((int)ncols < Npad) ncols <<= 1;
+      const size_t smem = (size_t)kTcRows * I * 2 + (size_t)Npad * I * 2 + 16;
+      static cudaError_t ae = cudaFuncSetAttribute(k_mm_fwd_tc<SY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   96 * 1024);
+      if (ae != cudaSuccess) return ae;
+      const long ntiles = (rows + kTcRows - 1) / kTcRows;
+      const int grid = (int)std::min<long>(ntiles, 3L * std::max(f->nsm, 1));
+      int* err = nullptr;
+      cudaError_t e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&err), f->tc_err, 0);
+      if (e != cudaSuccess) return e;
+      k_mm_fwd_tc<SY><<<grid, kTcRows, smem, f->stream>>>(X, I, Mt, bias, add, Ypre, Yact, Yf, O, Npad, ncols, rows,
+                                                          xgelu, ygelu, err);
+      return cudaGetLastError();
+    }
+  }
+  k_mm_fwd<SX, SY, float><<<grid_for(rows * O), 256, 0, f->stream>>>(X, I, Mt, bias, add, Ypre, Yact, Yf, O, rows,
+                                                                     xgelu, ygelu);
+  return cudaGetLastError();
+}
+
 template <typename S> ie_status fwd_impl(ie_fno* f, int B, const float* a, float* u) {
   using CS = typename Cx<S>::type;
+  if (f->tc_err && *reinterpret_cast<volatile int*>(f->tc_err)) {
+    *f->tc_err = 0;
+    f->err = "a tensor-core kernel's wait for its MMAs reached its limit";
+    return IE_ECUDA;
+  }
   const long rows = f->rows(B);
   const int C = f->C;
   const float* P = f->params + f->off[0];
@@ -494,22 +647,16 @@ template <typename S> ie_status fwd_impl(ie_fno* f, int B, const float* a, float
     FCK(cudaGetLastError());
     FCK(inverse_T(f, B, f->Wm, f->kbuf, 1, 1.f / ((float)f->N * f->N * f->N)));
     const bool last = (l == f->L - 1);
-    k_mm_fwd<S, S, float><<<grid_for(rows * C), 256, 0, f->stream>>>(
-        vl, C, f->params + f->off[2 + l], f->params + f->off[2 + f->L + l], f->kbuf, act<S>(f, f->pre, l, B, C),
-        act<S>(f, f->v, l + 1, B, C), nullptr, C, rows, 0, last ? 0 : 1);
-    FCK(cudaGetLastError());
+    FCK((mm_fwd<S, S>(f, vl, C, f->params + f->off[2 + l], f->params + f->off[2 + f->L + l], f->kbuf,
+                     act<S>(f, f->pre, l, B, C), act<S>(f, f->v, l + 1, B, C), nullptr, C, rows, 0, last ? 0 : 1)));
   }
   const long oQ1 = f->off[2 + 3 * f->L];
   // head: hp = v_L Q1 + q1 ; u = GELU(hp) Q2 + q2
-  k_mm_fwd<S, S, float><<<grid_for(rows * f->H), 256, 0, f->stream>>>(
-      act<S>(f, f->v, f->L, B, C), C, f->params + oQ1, f->params + oQ1 + (long)C * f->H, nullptr,
-      reinterpret_cast<S*>(f->hp), nullptr, nullptr, f->H, rows, 0, 0);
-  FCK(cudaGetLastError());
+  FCK((mm_fwd<S, S>(f, act<S>(f, f->v, f->L, B, C), C, f->params + oQ1, f->params + oQ1 + (long)C * f->H, nullptr,
+                   reinterpret_cast<S*>(f->hp), nullptr, nullptr, f->H, rows, 0, 0)));
   const long oQ2 = oQ1 + (long)C * f->H + f->H;
-  k_mm_fwd<S, float, float><<<grid_for(rows * f->Cout), 256, 0, f->stream>>>(
-      reinterpret_cast<S*>(f->hp), f->H, f->params + oQ2, f->params + oQ2 + (long)f->H * f->Cout, nullptr, nullptr,
-      nullptr, u, f->Cout, rows, 1, 0);
-  FCK(cudaGetLastError());
+  FCK((mm_fwd<S, float>(f, reinterpret_cast<S*>(f->hp), f->H, f->params + oQ2, f->params + oQ2 + (long)f->H * f->Cout,
+                       nullptr, nullptr, nullptr, u, f->Cout, rows, 1, 0)));
   return IE_OK;
 }
 
@@ -631,7 +778,24 @@ ie_status ie_fno_create(int32_t n, int32_t modes, int32_t width, int32_t layers,
     delete f;
     return IE_ENOMEM;
   }
+  if (cudaHostAlloc(reinterpret_cast<void**>(&f->tc_err), sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+    f->tc_err = nullptr;
+    delete f;
+    return IE_ENOMEM;
+  }
+  *f->tc_err = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&f->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete f;
+    return IE_ECUDA;
+  }
   *out = f;
+  return IE_OK;
+}
+
+ie_status ie_fno_set_tensor_cores(ie_fno* f, int32_t on) {
+  if (!f || (on != 0 && on != 1)) return IE_EINVAL;
+  f->tensor_cores = on;
   return IE_OK;
 }
 

@@ -102,6 +102,7 @@ _SIGS = {
     "ie_fno_create": (ct.c_int, [ct.c_int32] * 9 + [ct.POINTER(_P)]),
     "ie_fno_param_count": (ct.c_int64, [_P]),
     "ie_fno_set_stream": (ct.c_int, [_P, _P]),
+    "ie_fno_set_tensor_cores": (ct.c_int, [_P, ct.c_int32]),
     "ie_fno_set_params": (ct.c_int, [_P, ct.POINTER(ct.c_float)]),
     "ie_fno_get_params": (ct.c_int, [_P, ct.POINTER(ct.c_float)]),
     "ie_fno_forward": (ct.c_int, [_P, ct.c_int32, _P, _P]),
@@ -400,6 +401,10 @@ class FNO:
     def set_stream(self, stream):
         handle = getattr(stream, "cuda_stream", stream)
         self._check(_lib.ie_fno_set_stream(self.ptr, _P(handle or 0)))
+
+    def set_tensor_cores(self, on: bool):
+        """ie_fno_set_tensor_cores: BF16 pointwise maps on the tcgen05 tensor cores (default) or CUDA cores."""
+        self._check(_lib.ie_fno_set_tensor_cores(self.ptr, int(bool(on))))
 
     def set_params(self, flat: np.ndarray):
         v = np.ascontiguousarray(flat, dtype=np.float32)

@@ -29,6 +29,9 @@ CASES = {
     "tiny": (8, 3, 4, 2, 3, 2, 5, 2),
     "warmstart-shape": (16, 4, 8, 3, 12, 6, 16, 2),
     "ragged": (12, 5, 6, 2, 12, 6, 7, 3),
+    # widths where the BF16 pointwise maps run on the tensor cores (the layers' 32 -> 32, the head's
+    # 32 -> 128 and 128 -> 6 maps; the lift, 12 -> 32, stays on the CUDA cores)
+    "tensor-core": (16, 4, 32, 2, 12, 6, 128, 3),
 }
 
 
@@ -87,6 +90,32 @@ def test_forward_and_gradients_match_oracle(env, case, bf16):
         off += ref.size
         assert _rel(got, ref) <= tol, (name, _rel(got, ref))
     assert off == g.size
+
+
+def test_tensor_core_maps_match_cuda_core_maps(env):
+    # the same BF16 network forward with the pointwise maps on the tcgen05 tensor cores and on the CUDA
+    # cores: they differ only by the BF16 rounding of the weights the tensor cores read (and the order
+    # of the FP32 sums), so the outputs agree to BF16 precision; both agree with the FP64 oracle
+    torch, ie = env
+    prm, a, _ = _setup("tensor-core", 5)
+    B = a.shape[0]
+    u_ref = ofno.forward(prm, a)
+    dev = torch.device("cuda", 0)
+    a_d = torch.from_numpy(a.astype(np.float32)).to(dev)
+    outs = {}
+    with _net(ie, "tensor-core", True) as net:
+        net.set_params(ie.fno_flat(prm.flat()))
+        for on in (False, True, True):  # the tensor-core path twice: it is deterministic
+            net.set_tensor_cores(on)
+            u_d = torch.full(u_ref.shape, float("nan"), dtype=torch.float32, device=dev)
+            net.forward(B, a_d, u_d)
+            torch.cuda.synchronize()
+            outs.setdefault(on, []).append(u_d.cpu().numpy())
+    cuda_core, tc = outs[False][0], outs[True][0]
+    assert np.all(np.isfinite(tc))
+    assert np.array_equal(outs[True][0], outs[True][1])
+    assert _rel(tc, cuda_core) <= 1e-2
+    assert _rel(tc, u_ref) <= 2e-2 and _rel(cuda_core, u_ref) <= 2e-2
 
 
 def ie_flat_parts(prm):
