@@ -7,6 +7,9 @@
         one restarted GMRES(30) run on a sub-domain of the 128x128x256 workload divided by `scale`
     python -m paper_2306_17537_gb300.kernel_cases solve    --scale 2
         one complete forward solve (Algorithm 1) of the same workload
+    python -m paper_2306_17537_gb300.kernel_cases fno      --n 64 [--reps 10]
+        forward passes of the warm-start network (4 layers, width 32, 12 modes, hidden 128, BF16, batch 8)
+        with the pointwise maps on the CUDA cores, then on the tensor cores (ie_fno_set_tensor_cores)
     python -m paper_2306_17537_gb300.kernel_cases large    --scale 1 [--position 5]
         one warm-up and one measured solve of the 256x256x512 benchmark model as bench.py solves it
         (flexible GMRES over concurrent block-Jacobi sweeps); prints the measured solve's launch count, so
@@ -40,7 +43,7 @@ def main(argv=None):
     from . import ie, inputs
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["matvec", "gmres", "solve", "batch", "large"])
+    ap.add_argument("case", choices=["matvec", "gmres", "solve", "batch", "large", "fno"])
     ap.add_argument("--position", type=int, default=5)
     ap.add_argument("--positions", type=int, default=8)
     ap.add_argument("--lanes", type=int, default=4)
@@ -123,6 +126,31 @@ def main(argv=None):
                          "max_rel_residual": max(r[1].final_rel_residual for r in res),
                          "gmres_iters": [r[1].gmres_iters_total for r in res]}
         ctx = next(iter(ctxs.values()))[0]
+    elif a.case == "fno":
+        from . import fno_warmstart
+
+        n, B = a.n, 8
+        with ie.FNO(n, modes=12, width=32, layers=4, cin=12, cout=6, hidden=128, batch_max=B, bf16=True) as net:
+            net.set_stream(stream)
+            net.set_params(fno_warmstart.init_flat(ie, n, 12, 32, 4, 128, 0))
+            x = torch.randn((B, n ** 3, 12), dtype=torch.float32, device=dev)
+            u = torch.empty((B, n ** 3, 6), dtype=torch.float32, device=dev)
+            res = {}
+            for on in (False, True):
+                net.set_tensor_cores(on)
+                net.forward(B, x, u)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(a.reps):
+                    net.forward(B, x, u)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res["tensor_cores" if on else "cuda_cores"] = {"ms_per_forward": e0.elapsed_time(e1) / a.reps,
+                                                               "u_norm": float(u.norm())}
+            out.update(res)
+        print(json.dumps(out))
+        return
     elif a.case == "large":
         wl = inputs.config5(0, a.position, scale=max(a.scale, 1))
         ctx = _ctx(wl.grid, wl.sigma0, wl.freq, wl.sigma6)
