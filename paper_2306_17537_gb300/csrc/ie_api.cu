@@ -746,9 +746,13 @@ struct GmresOut {
 // stopping on the relative residual |b - A x| / |b| (eq. 9).
 // x holds x0 on entry unless x0_zero. Workspace c->V holds m+1 basis vectors.
 constexpr double kReorthTol = 1e-3;
+// verify = false: when a cycle's Arnoldi estimate reaches tol, the solve ends there without the true
+// residual (one operator application) that otherwise confirms it and leaves b - A x in c->kt1; for
+// callers that use the result only as an inexact solve (the preconditioner sweeps of the outer Krylov
+// iteration).
 template <typename T>
 ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_zero, double tol, int m, int max_it,
-                GmresOut* out) {
+                GmresOut* out, bool verify = true) {
   const bool cgs2 = tol < kReorthTol;
   const long n = 3 * A.nb();
   cudaStream_t s = c->stream;
@@ -858,6 +862,12 @@ ie_status gmres(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>* x, bool x0_
     for (int i = 0; i < jd; ++i) c->hpin[i] = make_double2(y[i].real(), y[i].imag());
     CK(cudaMemcpyAsync(c->dy.as<double2>(), c->hpin, sizeof(double2) * jd, cudaMemcpyHostToDevice, s));
     KL(IE_K_KRYLOV_MISC, sizeof(C<T>) * (double)n * (jd + 2), Krylov<T>::combine(V, ld, jd, c->dy.as<double2>(), x, n, s));
+    const double est_rel = std::abs(g[jd]) / bnorm;
+    if (!verify && est_rel <= tol) {
+      out->rel = est_rel;
+      out->converged = true;
+      return IE_OK;
+    }
     CKS(A.apply(x, tmp));
     out->matvecs++;
     KL(IE_K_KRYLOV_MISC, 3.0 * sizeof(C<T>) * n, Krylov<T>::rsub(b, tmp, n, dn + 1, sc, s));
@@ -1478,7 +1488,7 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
       if (cfg.graph)
         CKS(gmres_graph<T>(c, A, rhs, dx, tol_i, cfg.restart, cfg.max_inner, &go));
       else
-        CKS(gmres<T>(c, A, rhs, dx, true, tol_i, cfg.restart, cfg.max_inner, &go));
+        CKS(gmres<T>(c, A, rhs, dx, true, tol_i, cfg.restart, cfg.max_inner, &go, !pre));
       if (keep_ae && !pre && go.iters > 0)  // A_ii delta = rhs - r, r = rhs - A x the final true residual
         KL(IE_K_FIELD, 96.0 * nb,
            launch_add_diff_c64(c->AEb.as<float2>() + ae_off[i], reinterpret_cast<const float2*>(rhs),
@@ -1597,7 +1607,8 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
         jp->st = make_block<T>(w, 0, w->nz, &A, cfg.contraction != 0);
         C<T>* rhs_w = w->kb.template as<C<T>>();
         C<T>* dx_w = w->kx.template as<C<T>>();
-        if (jp->st == IE_OK) jp->st = gmres<T>(w, A, rhs_w, dx_w, true, jp->tol, cfg.restart, cfg.max_inner, &jp->go);
+        if (jp->st == IE_OK)
+          jp->st = gmres<T>(w, A, rhs_w, dx_w, true, jp->tol, cfg.restart, cfg.max_inner, &jp->go, !pre);
         if (jp->st == IE_OK) jp->st = A.to_field(dx_w);
         if (jp->st == IE_OK && sync(w) != cudaSuccess) jp->st = fail(w, IE_ECUDA, "sub-domain solve on its stream");
       });
