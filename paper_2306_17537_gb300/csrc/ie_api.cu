@@ -1094,19 +1094,29 @@ ie_status gmres_graph_launch(ie_ctx* c, const BlockOp<T>& A, const C<T>* b, C<T>
   CK(c->kt1.ensure(sizeof(C<T>) * (size_t)n));
   CK(c->gm_state.ensure(sizeof(GmState)));
   for (int k = 0; k < 3; ++k) CKS(cap_stream(c, k));
-  // outside any capture: allocates the block's workspaces and tunes its tiles
   C<T>* V = c->V.as<C<T>>();
-  CKS(A.apply(V, V + ld));
   const bool f32 = std::is_same<T, float>::value;
-  const std::vector<const void*> key = {
-      reinterpret_cast<const void*>(sizeof(C<T>)), reinterpret_cast<const void*>((long)A.z0),
-      reinterpret_cast<const void*>((long)A.nz), reinterpret_cast<const void*>((long)A.contract),
-      reinterpret_cast<const void*>((long)m), reinterpret_cast<const void*>((long)cgs2), b, x, V,
-      reinterpret_cast<const void*>(ld), c->kt1.p, (f32 ? c->A32 : c->A64).p, (f32 ? c->B32 : c->B64).p,
-      (f32 ? c->cw32 : c->cw64).p, A.S, c->gm_state.p, c->dh.p, c->part.p};
+  // the graph is keyed by everything its kernel arguments point at
+  auto make_key = [&]() {
+    return std::vector<const void*>{
+        reinterpret_cast<const void*>(sizeof(C<T>)), reinterpret_cast<const void*>((long)A.z0),
+        reinterpret_cast<const void*>((long)A.nz), reinterpret_cast<const void*>((long)A.contract),
+        reinterpret_cast<const void*>((long)m), reinterpret_cast<const void*>((long)cgs2), b, x, V,
+        reinterpret_cast<const void*>(ld), c->kt1.p, (f32 ? c->A32 : c->A64).p, (f32 ? c->B32 : c->B64).p,
+        (f32 ? c->cw32 : c->cw64).p, A.S, c->gm_state.p, c->dh.p, c->part.p};
+  };
+  std::vector<const void*> key = make_key();
   GmGraph* G = nullptr;
   for (auto* g : c->gm_graphs)
     if (g->key == key) G = g;
+  if (!G) {
+    // outside any capture: allocates the block's workspaces and tunes its tiles before they are captured
+    // (and may move the workspaces, so the key is taken again)
+    CKS(A.apply(V, V + ld));
+    key = make_key();
+    for (auto* g : c->gm_graphs)
+      if (g->key == key) G = g;
+  }
   if (!G) {
     G = new (std::nothrow) GmGraph();
     if (!G) return fail(c, IE_ENOMEM, "graph cache");
