@@ -182,6 +182,21 @@ __global__ void k_mm_fwd(const SX* __restrict__ X, int I, const float* __restric
     if (Yf) Yf[idx] = acc;
   }
 }
+// 16 consecutive values, 16-byte aligned: BF16 as two 16-byte stores, FP32 as four
+__device__ __forceinline__ void st16(__nv_bfloat16* p, const float (&v)[16]) {
+  uint4 q[2];
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(q);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) h[j] = __float22bfloat162_rn(make_float2(v[2 * j], v[2 * j + 1]));
+  reinterpret_cast<uint4*>(p)[0] = q[0];
+  reinterpret_cast<uint4*>(p)[1] = q[1];
+}
+__device__ __forceinline__ void st16(float* p, const float (&v)[16]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    reinterpret_cast<float4*>(p)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+}
+
 // The same map on the tensor cores, for BF16 X with I a multiple of 16 (16 <= I <= 128) and O <= 128:
 // tcgen05 MMAs of kind::f16 (BF16 operands, FP32 accumulation in tensor memory), M = 128 rows per tile,
 // N = O rounded up to 16, K = 16 per instruction. A persistent block of 128 threads keeps Mt (BF16,
@@ -268,7 +283,30 @@ __global__ void __launch_bounds__(kTcRows) k_mm_fwd_tc(const __nv_bfloat16* __re
       float d[16];
       __syncwarp();  // the warp-wide (aligned) load runs converged
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, d);
-      if (r < rows) {
+      if (r < rows && O % 16 == 0) {  // 16 whole columns: vector loads and stores (16-byte aligned)
+        const long idx = r * O + c0;
+        float acc[16], act16[16];
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          const float4 bv = *reinterpret_cast<const float4*>(bias + c0 + j);
+          acc[j] = d[j] + bv.x;
+          acc[j + 1] = d[j + 1] + bv.y;
+          acc[j + 2] = d[j + 2] + bv.z;
+          acc[j + 3] = d[j + 3] + bv.w;
+          if (add) {
+            const float4 av = *reinterpret_cast<const float4*>(add + idx + j);
+            acc[j] += av.x;
+            acc[j + 1] += av.y;
+            acc[j + 2] += av.z;
+            acc[j + 3] += av.w;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) act16[j] = ygelu ? gelu(acc[j]) : acc[j];
+        if (Ypre) st16(Ypre + idx, acc);
+        if (Yact) st16(Yact + idx, act16);
+        if (Yf) st16(Yf + idx, acc);
+      } else if (r < rows) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int o = c0 + j;
