@@ -456,7 +456,10 @@ def run_gb300(args):
     tr = traffic_record(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                # DRAM bytes per launch: the captured launch's DRAM-to-algorithmic ratio times this class's mean
+                # algorithmic bytes per launch (the capture is of the sub-domain launch; see profiles/traffic.json)
+                "traffic": (round(tr["dram_per_algorithmic_byte"] * by / max(launches, 1)) if tr else None),
+                "traffic_capture": (tr["workload"] if tr else None),
                 "algorithmic_bytes_per_launch": by / max(launches, 1), "avg_launch_us": 1e3 * ms / max(launches, 1),
                 "launches": launches}
     total_ms = sum(v[1] for v in prof.values())
