@@ -7,7 +7,9 @@ form), complex128 and double-float (the FP64-accurate whole-grid residual). Refe
   * 256 x 256 slabs: the oracle's direct summation at sampled cells (a full oracle FFT of the padded
     512 x 512 grid per component is too large for a test);
   * 512-cell-high columns: the oracle's FFT operator on the whole output, itself pinned to direct
-    summation, plus sampled direct sums.
+    summation, plus sampled direct sums;
+  * 512-cell-long x or y extents (the largest the ABI accepts: pencils of 1024) and a ragged 300 x 257
+    cross-section: the oracle's FFT operator on the whole output.
 Tolerances: 1e-5 relative (complex64), 1e-11 relative (complex128, double-float).
 """
 import numpy as np
@@ -98,3 +100,25 @@ def test_z_pencils_1024(ie, tall_column, form, precision, tol):
     picks = picks_for(g.n, 8)
     direct = sampled_reference(s6, x, picks, form == "contraction")
     assert np.max(np.abs(y.reshape(3, -1)[:, picks].T - direct)) <= max(tol, 1e-10) * np.max(np.abs(direct))
+
+
+@pytest.mark.parametrize("shape", [(6, 9, 512), (5, 512, 7), (3, 300, 257)])
+def test_longest_xy_pencils_and_ragged_sizes(ie, shape):
+    # the ABI's largest x and y extents (512 cells: padded pencils of 1024) and a ragged 300/257 case
+    # (pencils of 1024 and 512 with most of the padding), all precisions, against the oracle's FFT
+    # operator on the whole output
+    nz, ny, nx = shape
+    g = inputs.Grid(nx, ny, nz, H, (-nx * H / 2 + 0.03, -ny * H / 2 - 0.07, -nz * H / 2 + 0.11))
+    s6 = inputs.random_contrast_sigma6(shape, 21, S0, 1.5)
+    x = inputs.random_field((3,) + shape, 22)
+    ref = oop.FFTOperator(oop.contrast(s6, S0), H, F, S0)(x)
+    refc = oc.ContractionOperator(s6, H, F, S0)(x)
+    pad = lambda n: 1 << (2 * n - 1).bit_length()
+    with ie.Context(g, H, S0, F) as ctx:
+        assert ctx.fft_dims() == (pad(nx), pad(ny), pad(nz))
+        ctx.set_contrast(s6)
+        for prec, tol in ((ie.IE_PREC_MIXED, 1e-5), (ie.IE_PREC_FP64, 1e-11), (ie.IE_PREC_DFLOAT, 1e-11)):
+            y = ctx.matvec(x, precision=prec)
+            assert np.linalg.norm(y - ref) <= tol * np.linalg.norm(ref), prec
+        yc = ctx.matvec_contraction(x, precision=ie.IE_PREC_MIXED)
+        assert np.linalg.norm(yc - refc) <= 1e-5 * np.linalg.norm(refc)
