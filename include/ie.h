@@ -291,10 +291,11 @@ ie_status ie_profile_read(const ie_ctx* ctx, int32_t kclass, int64_t* launches, 
 
 /* Tile shapes chosen so far by the FFT-tile autotuner of this process, as text (one line per pass
  * shape: pass, element bytes, pencil length, Lx, Ly, slab heights, chosen variant, then the measured
- * microseconds per launch of every variant; variants 0/1/2 of the y passes and 0/1/4/6 of the z pass
- * are tiles of about 256 (z: 128), half, twice (and z: four times) as many threads, z-pass variants
- * 2/3/5/7 the same four with TMA staging of their input). Writes at most len bytes including the terminating NUL; returns the length the
- * full text needs. */
+ * microseconds per launch of every variant). Variants 0/1/2 of the y passes and 0/1/4/6 of the z pass
+ * are tiles of about 256 (z: 128), half, twice (and z: four times) as many threads; z-pass variants
+ * 2/3/5/7 are the same four with TMA staging of their input; z-pass variants 8/9 (256 threads) and
+ * 10/11 (512 threads) pair each row ky with its mirror Ly - ky, without and with TMA staging.
+ * Writes at most len bytes including the terminating NUL; returns the length the full text needs. */
 int32_t ie_tuned_tiles(char* buf, int32_t len);
 
 /* Testing hook (an extension of this library; the paper has no counterpart): after `after` more

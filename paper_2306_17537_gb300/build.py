@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libie_gb300.so")
-SOURCES = ["conv_f32.cu", "conv_f64.cu", "conv_df.cu", "green.cu", "krylov.cu", "ie_api.cu", "fno.cu"]
+SOURCES = ["conv_f32.cu", "conv_f32_p3.cu", "conv_f64.cu", "conv_f64_p3.cu", "conv_df.cu", "conv_df_p3.cu",
+           "green.cu", "krylov.cu", "ie_api.cu", "fno.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

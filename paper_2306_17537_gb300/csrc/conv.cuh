@@ -9,7 +9,7 @@ enum Epilogue { EPI_APPLY = 0, EPI_ACCUM128 = 1, EPI_RESID128 = 2, EPI_CONV = 3 
 
 bool supported_pencil(int L);
 constexpr int kTileVariants = 3;    // P2, P4
-constexpr int kP3TileVariants = 8;  // P3 (see ConvLaunch::p3)
+constexpr int kP3TileVariants = 12;  // P3 (see ConvLaunch::p3)
 
 template <typename T> struct ConvLaunch {
   // mt != nullptr: contraction form (ds = dsigma M, mt = M); also stores w = M x at stride w_cs
@@ -24,7 +24,9 @@ template <typename T> struct ConvLaunch {
                            int n_in, C<T>* out, long out_cs, long out_zs, long out_es, int n_out, int nlanes,
                            int nbatch, int ncomp, const C<T>* tw, cudaStream_t s);
   // variant: tiles of about 128 (0), 64 (1), 256 (4) and 512 (6) threads, and the same with TMA staging
-  // of the input pencils (2, 3, 5, 7);
+  // of the input pencils (2, 3, 5, 7); 256 and 512 threads with mirrored rows ky, Ly - ky (8, 10) and
+  // the same with TMA staging (9, 11). Variants 8 and 9 exist for float only: for the other types
+  // they return cudaErrorNotSupported without launching (the autotuner skips them);
   // err: set to 1 (device) if a staging wait of a TMA variant gave up
   static cudaError_t p3(int L, int variant, const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs,
                         int nzt, int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err, cudaStream_t s);

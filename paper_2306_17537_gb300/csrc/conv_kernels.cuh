@@ -171,14 +171,19 @@ __global__ void __launch_bounds__(LaneCfg<T, L, NT>::NTH) k_lanes_fft(
 // component's FFT exchanges), so a thread holds one pencil in registers at a time. A block is W
 // neighbouring lanes kx (W = NT / TT for about NT threads): wider tiles give longer contiguous row
 // segments in B and in the Green octant, narrower ones more blocks per SM; the autotuner chooses.
-template <typename T, int L, int NT = 128> struct P3Cfg {
+// Mirrored tiles (MIR) split the W lanes into two rows of W/2: row ky and its mirror Ly - ky (0 with
+// Ly/2). Both rows read the same Green octant column (|ky| is the same), so a warp loads each octant
+// value once for two pencils and the octant is not fetched a second time for the mirrored row.
+template <typename T, int L, int NT = 128, bool MIR = false> struct P3Cfg {
   static constexpr int TT = Plan<T, L>::TT;
   static constexpr int W0 = NT / TT;
   static constexpr int W = W0 < 1 ? 1 : (W0 > 32 ? 32 : W0);
   static constexpr int NTH = W * TT;                 // threads launched per block
   static constexpr int MINB = NTH >= 512 ? 1 : 512 / NTH;  // blocks per SM the register budget is set for
-  // TMA staging of the input pencils needs box rows of a multiple of 16 bytes (W lanes per row)
-  static constexpr bool kTmaOk = (W * (int)sizeof(C<T>)) % 16 == 0;
+  static constexpr bool kMir = MIR && W >= 2;
+  static constexpr int WH = kMir ? W / 2 : W;  // lanes per y row
+  // TMA staging of the input pencils needs box rows of a multiple of 16 bytes (WH lanes per row)
+  static constexpr bool kTmaOk = (WH * (int)sizeof(C<T>)) % 16 == 0;
   static constexpr int BZ = L < 256 ? L : 256;  // rows per TMA box (the box limit is 256)
   static constexpr size_t kSpecBytes = 3 * (size_t)L * W * sizeof(C<T>);
   // spectra + 3 mbarriers + room to align the spectra (and TMA destinations) to 128 bytes
@@ -190,22 +195,26 @@ template <typename T, int L, int NT = 128> struct P3Cfg {
 // asynchronous tensor copies issued at kernel start, so the loads of components 1 and 2 overlap the FFT
 // of component 0. Otherwise each component is loaded into registers just before its FFT. A staging
 // wait that exceeds its spin limit sets *err, waits (bounded) for the other copies and ends the block.
-template <typename T, int L, int NT, bool TMA>
-__global__ void __launch_bounds__(P3Cfg<T, L, NT>::NTH, P3Cfg<T, L, NT>::MINB) k_p3_spectral(
+template <typename T, int L, int NT, bool TMA, bool MIR>
+__global__ void __launch_bounds__(P3Cfg<T, L, NT, MIR>::NTH, P3Cfg<T, L, NT, MIR>::MINB) k_p3_spectral(
     const C<T>* __restrict__ Bin, long in_cs, int nzs, int os, C<T>* __restrict__ Bout, long out_cs,
     int nzt, int ot, const C<T>* __restrict__ G, int Lx, int Ly, const C<T>* __restrict__ tw,
     const __grid_constant__ CUtensorMap tmap, int* __restrict__ err) {
-  using Cfg = P3Cfg<T, L, NT>;
-  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = Cfg::W;
-  constexpr bool kTma = TMA && Cfg::kTmaOk;
+  using Cfg = P3Cfg<T, L, NT, MIR>;
+  constexpr int E = Plan<T, L>::E, TT = Plan<T, L>::TT, W = Cfg::W, WH = Cfg::WH;
+  constexpr bool kTma = TMA && Cfg::kTmaOk, kMir = Cfg::kMir;
   extern __shared__ __align__(128) unsigned char p3_dyn[];
   unsigned char* sbase = p3_dyn + ((128u - (smem_addr(p3_dyn) & 127u)) & 127u);
   C<T>* spec_base = reinterpret_cast<C<T>*>(sbase);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sbase + Cfg::kSpecBytes);
   (void)bar;
+  // spectrum c of the block: [row half][position][WH lanes]; this thread's column is lane l of half h
   auto spec = [spec_base](int c) { return spec_base + c * (L * W); };
   const int w = threadIdx.x, t = threadIdx.y;
-  const int kx = blockIdx.x * W + w, ky = blockIdx.y;
+  const int h = kMir ? w / WH : 0, l = kMir ? w % WH : w;
+  const int ky_mirror = blockIdx.y == 0 ? Ly / 2 : Ly - (int)blockIdx.y;
+  const int kx = blockIdx.x * WH + l, ky = h == 0 ? (int)blockIdx.y : ky_mirror;
+  auto col = [&](int c) { return spec(c) + h * (L * WH) + l; };
   const bool act = kx < Lx;
   const long plane = (long)Ly * Lx, off = (long)ky * Lx + kx;
   C<T> v[E];
@@ -220,16 +229,17 @@ __global__ void __launch_bounds__(P3Cfg<T, L, NT>::NTH, P3Cfg<T, L, NT>::MINB) k
       constexpr int R = (int)sizeof(C<T>) / 8;  // 8-byte tensor elements per complex value
       for (int c = 0; c < 3; ++c) {
         mbar_expect_tx(bar + c, (unsigned)(L * W * sizeof(C<T>)));
-        for (int k = 0; k < L / Cfg::BZ; ++k)
-          tma_load_4d(spec(c) + (size_t)k * Cfg::BZ * W, &tmap, (int)blockIdx.x * W * R, ky, k * Cfg::BZ - os, c,
-                      bar + c);
+        for (int hh = 0; hh < (kMir ? 2 : 1); ++hh)
+          for (int k = 0; k < L / Cfg::BZ; ++k)
+            tma_load_4d(spec(c) + (size_t)hh * L * WH + (size_t)k * Cfg::BZ * WH, &tmap, (int)blockIdx.x * WH * R,
+                        hh == 0 ? (int)blockIdx.y : ky_mirror, k * Cfg::BZ - os, c, bar + c);
       }
     }
   }
   // forward z-FFT of each component; spectrum left in spec[c] at the thread's own positions
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
-    LaneSM<T, W> sm{spec(c) + w};
+    LaneSM<T, WH> sm{col(c)};
     if constexpr (kTma) {
       if (!__syncthreads_and(mbar_wait(bar + c, 0))) {
         if (t == 0 && w == 0) {
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(P3Cfg<T, L, NT>::NTH, P3Cfg<T, L, NT>::MINB) k
         return;
       }
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = spec(c)[(t + TT * m) * W + w];  // staged rows are dense
+      for (int m = 0; m < E; ++m) v[m] = col(c)[(t + TT * m) * WH];  // staged rows are dense
       __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]
     } else {
 #pragma unroll
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(P3Cfg<T, L, NT>::NTH, P3Cfg<T, L, NT>::MINB) k
     const int ix = xlo ? kx : Lx - kx, iy = ylo ? ky : Ly - ky;
     const bool nxy = xlo != ylo;
     const C<T>* gb = G + (long)iy * ox + ix;
-    LaneSM<T, W> s0{spec(0) + w}, s1{spec(1) + w}, s2{spec(2) + w};
+    LaneSM<T, WH> s0{col(0)}, s1{col(1)}, s2{col(2)};
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const bool zlo = (E == 1) || (m < E / 2);  // lower half of kz: s_z = +1
@@ -284,7 +294,7 @@ __global__ void __launch_bounds__(P3Cfg<T, L, NT>::NTH, P3Cfg<T, L, NT>::MINB) k
   // inverse z-FFT of each component and crop
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
-    LaneSM<T, W> sm{spec(c) + w};
+    LaneSM<T, WH> sm{col(c)};
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = sm.ld(t + TT * m);
     __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]

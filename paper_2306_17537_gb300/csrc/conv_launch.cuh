@@ -163,33 +163,35 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // TMA = true stages the input pencils with tensor copies when the tile allows it (P3Cfg::kTmaOk) and
 // the CUDA driver provides the tensor-map encoder; otherwise the same tile runs with register loads.
+// MIR = true pairs each row ky with its mirror (P3Cfg::kMir; a one-lane tile runs unpaired).
 // Every tile keeps its spectra in dynamic shared memory (above the 48 KB default for the wider tiles).
-template <typename T, int N, int NT, bool TMA>
+template <typename T, int N, int NT, bool TMA, bool MIR>
 static cudaError_t p3_run(const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt, int ot,
                           const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err, const CUtensorMap& map,
                           cudaStream_t s) {
-  using Cfg = P3Cfg<T, N, NT>;
+  using Cfg = P3Cfg<T, N, NT, MIR>;
   static std::once_flag attr;
   static cudaError_t ae = cudaSuccess;
   std::call_once(attr, [] {
     if (Cfg::kSmem > 48 * 1024)
-      ae = cudaFuncSetAttribute(k_p3_spectral<T, N, NT, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      ae = cudaFuncSetAttribute(k_p3_spectral<T, N, NT, TMA, MIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Cfg::kSmem);
   });
   if (ae != cudaSuccess) return ae;
-  dim3 blk(Cfg::W, Plan<T, N>::TT), grd((unsigned)((Lx + Cfg::W - 1) / Cfg::W), (unsigned)Ly);
-  k_p3_spectral<T, N, NT, TMA><<<grd, blk, Cfg::kSmem, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw,
-                                                            map, err);
+  const unsigned gy = Cfg::kMir ? (unsigned)(Ly / 2) : (unsigned)Ly;
+  dim3 blk(Cfg::W, Plan<T, N>::TT), grd((unsigned)((Lx + Cfg::WH - 1) / Cfg::WH), gy);
+  k_p3_spectral<T, N, NT, TMA, MIR><<<grd, blk, Cfg::kSmem, s>>>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx,
+                                                                 Ly, tw, map, err);
   return cudaGetLastError();
 }
 
-template <typename T, int N, int NT, bool TMA>
+template <typename T, int N, int NT, bool TMA, bool MIR = false>
 static cudaError_t p3_launch(const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout, long out_cs, int nzt, int ot,
                              const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err, cudaStream_t s) {
-  using Cfg = P3Cfg<T, N, NT>;
-  constexpr int W = Cfg::W;
+  using Cfg = P3Cfg<T, N, NT, MIR>;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
+  if (Cfg::kMir && Ly % 2 != 0) return cudaErrorInvalidValue;  // padded lengths are even
   if constexpr (TMA && Cfg::kTmaOk) {
     auto enc = tensor_map_encoder();
     if (enc) {
@@ -197,40 +199,56 @@ static cudaError_t p3_launch(const C<T>* Bin, long in_cs, int nzs, int os, C<T>*
       constexpr int R = (int)sizeof(C<T>) / 8;
       const cuuint64_t dims[4] = {(cuuint64_t)Lx * R, (cuuint64_t)Ly, (cuuint64_t)nzs, 3};
       const cuuint64_t strides[3] = {(cuuint64_t)Lx * R * 8, (cuuint64_t)Ly * Lx * R * 8, (cuuint64_t)in_cs * R * 8};
-      const cuuint32_t box[4] = {(cuuint32_t)(W * R), 1, (cuuint32_t)Cfg::BZ, 1};
+      const cuuint32_t box[4] = {(cuuint32_t)(Cfg::WH * R), 1, (cuuint32_t)Cfg::BZ, 1};
       const cuuint32_t estr[4] = {1, 1, 1, 1};
       if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<C<T>*>(Bin), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-      return p3_run<T, N, NT, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, map, s);
+      return p3_run<T, N, NT, true, MIR>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, map, s);
     }
   }
-  return p3_run<T, N, NT, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, map, s);
+  return p3_run<T, N, NT, false, MIR>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, map, s);
 }
+
+// The mirrored 256-thread tiles (variants 8, 9) are built for float only: the complex64 operator runs
+// on sub-domains of every shape, the complex128 and double-float ones mostly on the whole grid, where
+// the 512-thread tiles win, and each further instantiation lengthens the build of those units.
+template <typename T> constexpr bool kMir256 = std::is_same<T, float>::value;
 
 template <typename T>
 cudaError_t ConvLaunch<T>::p3(int L, int variant, const C<T>* Bin, long in_cs, int nzs, int os, C<T>* Bout,
                               long out_cs, int nzt, int ot, const C<T>* G, int Lx, int Ly, const C<T>* tw, int* err,
                               cudaStream_t s) {
+#define IE_P3(N, NT, TMA, MIR) \
+  p3_launch<T, N, NT, TMA, MIR>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s)
   switch (L) {
-#define IE_CASE(N)                                                                                                  \
-  case N:                                                                                                           \
-    switch (variant) {                                                                                              \
-      case 1: return p3_launch<T, N, 64, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
-      case 2: return p3_launch<T, N, 128, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
-      case 3: return p3_launch<T, N, 64, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);   \
-      case 4: return p3_launch<T, N, 256, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
-      case 5: return p3_launch<T, N, 256, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
-      case 6: return p3_launch<T, N, 512, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s); \
-      case 7: return p3_launch<T, N, 512, true>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);  \
-      default: return p3_launch<T, N, 128, false>(Bin, in_cs, nzs, os, Bout, out_cs, nzt, ot, G, Lx, Ly, tw, err, s);\
+#define IE_CASE(N)                                                                  \
+  case N:                                                                           \
+    switch (variant) {                                                              \
+      case 1: return IE_P3(N, 64, false, false);                                    \
+      case 2: return IE_P3(N, 128, true, false);                                    \
+      case 3: return IE_P3(N, 64, true, false);                                     \
+      case 4: return IE_P3(N, 256, false, false);                                   \
+      case 5: return IE_P3(N, 256, true, false);                                    \
+      case 6: return IE_P3(N, 512, false, false);                                   \
+      case 7: return IE_P3(N, 512, true, false);                                    \
+      case 8:                                                                       \
+        if constexpr (kMir256<T>) return IE_P3(N, 256, false, true);                \
+        else return cudaErrorNotSupported;                                          \
+      case 9:                                                                       \
+        if constexpr (kMir256<T>) return IE_P3(N, 256, true, true);                 \
+        else return cudaErrorNotSupported;                                          \
+      case 10: return IE_P3(N, 512, false, true);                                   \
+      case 11: return IE_P3(N, 512, true, true);                                    \
+      default: return IE_P3(N, 128, false, false);                                  \
     }
     IE_FOR_EACH_L(IE_CASE)
 #undef IE_CASE
     default:
       return cudaErrorInvalidValue;
   }
+#undef IE_P3
 }
 
 template <typename T>

@@ -83,12 +83,15 @@ template <typename T> struct RowSM {
   __host__ __device__ static constexpr int words(int L) { return L + L / 16; }
 };
 // W side-by-side pencils (lanes contiguous in memory): element i of lane w at [i][w]. When a row of W
-// elements is half a 128-byte bank line, rows are swapped in pairs every 16 rows so that the stage
-// writes of neighbouring threads fall into different halves of the line.
+// elements is narrower than a 128-byte bank line (RPL rows per line), row i is stored at i XOR
+// ((i / 16) mod RPL): the first stage writes rows 16 apart from neighbouring threads of a warp, and
+// the XOR spreads them over the line (a permutation inside each aligned group of 16 rows, so runs of
+// consecutive rows stay on distinct banks).
 template <typename T, int W> struct LaneSM {
   C<T>* base;  // already offset by the lane
-  static constexpr bool kSwz = (W * (int)sizeof(C<T>) == 64);
-  __device__ __forceinline__ int row(int i) const { return kSwz ? (i ^ ((i >> 4) & 1)) : i; }
+  static constexpr int kRowBytes = W * (int)sizeof(C<T>);
+  static constexpr int RPL = kRowBytes < 128 ? 128 / kRowBytes : 1;
+  __device__ __forceinline__ int row(int i) const { return RPL > 1 ? (i ^ ((i >> 4) & (RPL - 1))) : i; }
   __device__ __forceinline__ C<T> ld(int i) const { return base[row(i) * W]; }
   __device__ __forceinline__ void st(int i, C<T> x) const { base[row(i) * W] = x; }
 };
@@ -98,6 +101,33 @@ __device__ __forceinline__ C<T> twiddle(const C<T>* __restrict__ tw, int idx) {
   C<T> w = ldgv(tw + idx);
   if (SIGN > 0) w.y = -w.y;
   return w;
+}
+
+// Butterfly twiddles p[r] = w^r (r = 1..R-1), w = exp(SIGN 2 pi i q / TWN) for the table index q of r = 1.
+// In float only the power-of-two entries w, w^2, w^4, w^8 are loaded and the others formed as products
+// of those (r's binary digits): at most four rounded table entries and three roundings per twiddle, a
+// few float ulps, and a third to a quarter of the table loads, which share the load/store pipe with the
+// shared-memory exchanges. In double and double-float every twiddle is a table entry.
+template <typename T> struct TwiddlePowers { static constexpr bool v = false; };
+template <> struct TwiddlePowers<float> { static constexpr bool v = true; };
+
+template <typename T, int R, int SIGN>
+__device__ __forceinline__ void butterfly_twiddles(const C<T>* __restrict__ tw, int q, C<T> (&p)[R]) {
+  if constexpr (TwiddlePowers<T>::v) {
+#pragma unroll
+    for (int b = 1; b < R; b <<= 1) p[b] = twiddle<T, SIGN>(tw, q * b);
+#pragma unroll
+    for (int r = 3; r < R; ++r) {
+      if (r & (r - 1)) {
+        int hb = r;
+        while (hb & (hb - 1)) hb &= hb - 1;  // highest power of two in r
+        p[r] = cmul(p[hb], p[r - hb]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) p[r] = twiddle<T, SIGN>(tw, q * r);
+  }
 }
 
 template <typename T, int L, int SIGN, int NS, class SM> struct Stages {
@@ -126,8 +156,10 @@ template <typename T, int L, int SIGN, int NS, class SM> struct Stages {
       if constexpr (!FIRST) {
         const int j = t + TT * b;
         const int k = j & (NS - 1);
+        C<T> p[R];
+        butterfly_twiddles<T, R, SIGN>(tw, k * (TWN / (NS * R)), p);
 #pragma unroll
-        for (int r = 1; r < R; ++r) x[b][r] = cmul(x[b][r], twiddle<T, SIGN>(tw, k * r * (TWN / (NS * R))));
+        for (int r = 1; r < R; ++r) x[b][r] = cmul(x[b][r], p[r]);
       }
       DFT<T, R, SIGN>::run(x[b]);
     }

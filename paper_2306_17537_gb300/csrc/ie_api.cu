@@ -374,7 +374,8 @@ template <typename T> ie_status ensure_conv_ws(ie_ctx* c, int zcap) {
 // ------------------------------------------------------------------ FFT tile autotuner
 // The strided passes (P2, P3, P4) have three tile shapes: the default, one with half the pencils per
 // block and one with twice as many (P3 a fourth with four times as many); P3 has each also with TMA
-// staging of its input pencils (eight variants). The first convolution
+// staging of its input pencils, and its two widest tiles also with mirrored rows (twelve variants,
+// of which a precision may build fewer). The first convolution
 // of a new shape times every variant on the live buffers
 // (three timed launches each after a warm-up; the work is data independent) and keeps the fastest for
 // the rest of the process. Variants produce bit-identical results.
@@ -404,6 +405,11 @@ template <class F> cudaError_t tune(ie_ctx* c, const TuneKey& k, F&& run, int* b
   std::vector<float> times;
   for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
     e = run(v);  // warm-up (module load, caches)
+    if (e == cudaErrorNotSupported) {  // a tile this arithmetic does not build: nothing was launched
+      e = cudaSuccess;
+      times.push_back(INFINITY);
+      continue;
+    }
     if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
     for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = run(v);
     if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
@@ -2254,7 +2260,9 @@ int32_t ie_tuned_tiles(char* buf, int32_t len) {
       const auto it = g_tune_ms.find(k);
       if (it != g_tune_ms.end())
         for (size_t v = 0; v < it->second.size(); ++v)
-          txt += (v ? "/" : "") + std::to_string((int)std::lround(1000.0 * it->second[v]));
+          txt += (v ? "/" : "") + (std::isfinite(it->second[v])
+                                         ? std::to_string((int)std::lround(1000.0 * it->second[v]))
+                                         : std::string("-"));  // a variant this arithmetic does not build
       txt += "\n";
     }
   }
