@@ -248,8 +248,13 @@ __global__ void __launch_bounds__(P3Cfg<T, L, NT, MIR>::NTH, P3Cfg<T, L, NT, MIR
         }
         return;
       }
+      // staged rows are dense; positions outside the source slab hold the copy's zero fill and are
+      // not read back (half of every pencil for the usual 2n padding)
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = col(c)[(t + TT * m) * WH];  // staged rows are dense
+      for (int m = 0; m < E; ++m) {
+        const int z = t + TT * m - os;
+        v[m] = (z >= 0 && z < nzs) ? col(c)[(t + TT * m) * WH] : czero<C<T>>();
+      }
       __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]
     } else {
 #pragma unroll

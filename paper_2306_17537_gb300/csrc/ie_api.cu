@@ -18,6 +18,7 @@
 #include <complex>
 #include <cstddef>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1227,7 +1228,8 @@ struct SolveCfg {
 // FP64-accurate. Classical Gram-Schmidt with the DGKS second pass and FP64 Givens rotations on the host.
 // Each outer step costs one sweep, one whole-grid application and the orthogonalisation.
 template <typename T, typename VT, class Sweep>
-ie_status fgmres_outer(ie_ctx* c, const SolveCfg& cfg, const std::vector<char>& act, Sweep& sweep, double e0norm,
+ie_status fgmres_outer(ie_ctx* c, const SolveCfg& cfg, const std::vector<char>& act, Sweep& sweep,
+                       const std::function<ie_status(const float2*, float2*, double, int*)>& sweep64, double e0norm,
                        double* e, int* sweeps, ie_info* info, bool record, bool fast_ok) {
   constexpr bool f32 = std::is_same<VT, float>::value;
   using CV = C<VT>;
@@ -1294,12 +1296,20 @@ ie_status fgmres_outer(ie_ctx* c, const SolveCfg& cfg, const std::vector<char>& 
       CV* vj = V + (size_t)j * ld;
       CV* zj = Z + (size_t)j * ld;
       CV* w = V + (size_t)(j + 1) * ld;
-      CKS(to_field(vj, PR));
-      CK(cudaMemsetAsync(PZ, 0, sizeof(double2) * N3, s));
       int its = 0;
-      CKS(sweep(PR, PZ, cfg.outer_inner_tol, &its));
+      if constexpr (f32) {
+        if (sweep64) {  // z_j = M^-1 v_j straight between the complex64 outer vectors
+          CKS(mask(zj));
+          CKS(sweep64(reinterpret_cast<const float2*>(vj), reinterpret_cast<float2*>(zj), cfg.outer_inner_tol, &its));
+        }
+      }
+      if (!(f32 && sweep64)) {
+        CKS(to_field(vj, PR));
+        CK(cudaMemsetAsync(PZ, 0, sizeof(double2) * N3, s));
+        CKS(sweep(PR, PZ, cfg.outer_inner_tol, &its));
+        CKS(to_vec(PZ, zj));
+      }
       ++*sweeps;
-      CKS(to_vec(PZ, zj));
       if constexpr (f32)
         CKS(conv<float>(c, S, zj, c->N, 0, c->nz, 0, c->nz, 0, EPI_APPLY, zj, c->N, w, c->N, nullptr, 0, nullptr, 0));
       else
@@ -1537,8 +1547,13 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
   // block solves read only the previous sweep's field, so they are independent.
   const bool conc = cfg.concurrent && cfg.dd_mode == IE_DD_JACOBI && M > 1;
   if (conc) CKS(prepare_workers(c, cfg.split));
-  auto sweep_conc = [&](double2* Rb, double2* Eb, double precond_tol, int* sweep_its) -> ie_status {
+  // v64/z64 (complex64 preconditioner application of the outer Krylov iteration, z = M^-1 v with the
+  // whole-grid layout of the outer basis): each block's right-hand side is copied from v64's slab and its
+  // solution to z64's slab, with no complex128 field in between; Rb and Eb are then unused.
+  auto sweep_conc_io = [&](double2* Rb, double2* Eb, const float2* v64, float2* z64, double precond_tol,
+                           int* sweep_its) -> ie_status {
     const bool pre = precond_tol > 0;
+    const bool direct = v64 != nullptr && std::is_same<T, float>::value;
     struct Job {
       int i = 0;
       double tol = 0.0;
@@ -1550,6 +1565,18 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
       if (!blk_active[i]) continue;
       const BlockOp<T>& A = ops[i];
       const long nb = A.nb(), off = (long)A.z0 * nxy;
+      ie_ctx* w = c->workers[i];
+      if (direct) {  // a zero right-hand side gives a zero solution inside the block solve
+        CK(w->kb.ensure(sizeof(C<T>) * 3 * nb));
+        CK(w->kx.ensure(sizeof(C<T>) * 3 * nb));
+        CK(cudaMemcpy2DAsync(w->kb.p, sizeof(float2) * nb, v64 + off, sizeof(float2) * c->N, sizeof(float2) * nb, 3,
+                             cudaMemcpyDeviceToDevice, s));
+        Job j;
+        j.i = i;
+        j.tol = std::min(std::max(precond_tol, 1e-6), 0.5);
+        jobs.push_back(j);
+        continue;
+      }
       double2* Ri = Rb + off;
       double2* Ei = Eb + off;
       double rnorm;
@@ -1572,7 +1599,6 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
       double tol_i = pre ? precond_tol : (cfg.adaptive ? e / 10.0 : cfg.fixed_tol) * bnorm / rnorm;
       if (std::is_same<T, float>::value) tol_i = std::max(tol_i, 1e-6);
       tol_i = std::min(tol_i, 0.5);
-      ie_ctx* w = c->workers[i];
       CK(w->kb.ensure(sizeof(C<T>) * 3 * nb));
       CK(w->kx.ensure(sizeof(C<T>) * 3 * nb));
       if (std::is_same<T, float>::value)
@@ -1636,15 +1662,20 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
       ie_ctx* w = c->workers[job.i];
       fold_profile(c, w);
       const long nb = ops[job.i].nb(), off = (long)ops[job.i].z0 * nxy;
-      double2* Ei = Eb + off;
-      if (keep_ae && !pre && job.go.iters > 0)  // A_ii delta = rhs - r (r: the final true residual)
-        KL(IE_K_FIELD, 96.0 * nb,
-           launch_add_diff_c64(c->AEb.as<float2>() + ae_off[job.i], w->kb.as<float2>(), w->kt1.as<float2>(), 3 * nb,
-                               s));
-      if (std::is_same<T, float>::value)
-        KL(IE_K_FIELD, 120.0 * nb, launch_add_c64_to_c128(w->kx.as<float2>(), nb, Ei, c->N, nb, s));
-      else
-        KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(w->kx.as<double2>(), nb, Ei, c->N, nb, s));
+      if (direct) {
+        CK(cudaMemcpy2DAsync(z64 + off, sizeof(float2) * c->N, w->kx.p, sizeof(float2) * nb, sizeof(float2) * nb, 3,
+                             cudaMemcpyDeviceToDevice, s));
+      } else {
+        double2* Ei = Eb + off;
+        if (keep_ae && !pre && job.go.iters > 0)  // A_ii delta = rhs - r (r: the final true residual)
+          KL(IE_K_FIELD, 96.0 * nb,
+             launch_add_diff_c64(c->AEb.as<float2>() + ae_off[job.i], w->kb.as<float2>(), w->kt1.as<float2>(),
+                                 3 * nb, s));
+        if (std::is_same<T, float>::value)
+          KL(IE_K_FIELD, 120.0 * nb, launch_add_c64_to_c128(w->kx.as<float2>(), nb, Ei, c->N, nb, s));
+        else
+          KL(IE_K_FIELD, 144.0 * nb, launch_add_c128(w->kx.as<double2>(), nb, Ei, c->N, nb, s));
+      }
       inner_ok = inner_ok && job.go.converged;
       *sweep_its += job.go.iters;
       info->gmres_iters_total += job.go.iters;
@@ -1653,14 +1684,25 @@ ie_status solve_one(ie_ctx* c, const SolveCfg& cfg, ie_info* info, bool record) 
     }
     return IE_OK;
   };
+  auto sweep_conc = [&](double2* Rb, double2* Eb, double precond_tol, int* sweep_its) -> ie_status {
+    return sweep_conc_io(Rb, Eb, nullptr, nullptr, precond_tol, sweep_its);
+  };
   auto sweep_any = [&](double2* Rb, double2* Eb, double precond_tol, int* sweep_its) -> ie_status {
     return conc ? sweep_conc(Rb, Eb, precond_tol, sweep_its) : sweep(Rb, Eb, precond_tol, sweep_its);
   };
+  // complex64 preconditioner for the outer iteration (concurrent block Jacobi in complex64 only)
+  std::function<ie_status(const float2*, float2*, double, int*)> sweep64;
+  if (conc && std::is_same<T, float>::value)
+    sweep64 = [&](const float2* v, float2* z, double tol, int* its) -> ie_status {
+      return sweep_conc_io(nullptr, nullptr, v, z, tol, its);
+    };
   int sweeps = 0;
   if (cfg.outer_krylov && cfg.dd_mode != IE_DD_NONE) {
     const ie_status ost =
-        fast_ok ? fgmres_outer<T, float>(c, cfg, blk_active, sweep_any, e0norm, &e, &sweeps, info, record, fast_ok)
-                : fgmres_outer<T, double>(c, cfg, blk_active, sweep_any, e0norm, &e, &sweeps, info, record, fast_ok);
+        fast_ok ? fgmres_outer<T, float>(c, cfg, blk_active, sweep_any, sweep64, e0norm, &e, &sweeps, info, record,
+                                         fast_ok)
+                : fgmres_outer<T, double>(c, cfg, blk_active, sweep_any, sweep64, e0norm, &e, &sweeps, info, record,
+                                          fast_ok);
     CKS(ost);
   } else {
     while (e > cfg.tol && sweeps < cfg.max_outer) {
