@@ -512,7 +512,9 @@ def run_gb300(args):
         "matvec": {"sub_domain": [g.nx, g.ny, nzb], "ms": round(mv_ms, 4), "algorithmic_GB": round(mv_bytes / 1e9, 4),
                    "GBps": round(mv_bytes / 1e9 / (mv_ms / 1e3), 1),
                    "frac_of_peak": round(mv_bytes / 1e9 / (mv_ms / 1e3) / peak, 4),
-                   "bytes_per_voxel": round(mv_bytes / n_block, 1)},
+                   "bytes_per_voxel": round(mv_bytes / n_block, 1),
+                   # compulsory traffic of one application: read x and the contrast, the Green octant, write y
+                   "compulsory_GBps": round(120.0 * n_block / 1e9 / (mv_ms / 1e3), 1)},
         "solve": {"status": int(st), "all_steps_converged": not failed, "failed_steps": failed,
                   "profiled_pass": {"steps": prof_steps, "ms_per_step": round(p_ms / prof_steps, 2),
                                     "blocks": "one after another (per-launch events do not overlap)"},
