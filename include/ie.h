@@ -305,6 +305,15 @@ int32_t ie_tuned_tiles(char* buf, int32_t len);
  * failure returns IE_ENOMEM and leaves its context usable (nothing half-allocated is kept). */
 void ie_debug_fail_allocation(int32_t after);
 
+/* Testing hook (an extension of this library; the paper has no counterpart): every later convolution of
+ * this process runs pass `pass` (2 = the y pass P2, 3 = the z pass P3, 4 = the inverse y pass P4) in
+ * tile variant `variant` (the numbering of ie_tuned_tiles) instead of the autotuned one; -1 returns the
+ * pass to the autotuner. All variants compute bit-identical results, and this hook lets a test check
+ * that. A z-pass variant that the arithmetic in use does not build (8 and 9 outside complex64) makes the
+ * convolution fail with IE_ECUDA. IE_EINVAL for a pass or variant out of range. Not thread-safe with
+ * respect to convolutions in flight on other threads. */
+ie_status ie_debug_force_tile(int32_t pass, int32_t variant);
+
 /* Last error message of the context (never NULL; "" when none). */
 const char* ie_last_error(const ie_ctx* ctx);
 

@@ -390,7 +390,14 @@ std::map<TuneKey, int> g_tuned;
 std::map<TuneKey, std::vector<float>> g_tune_ms;  // mean time of one launch of each variant (ms)
 std::mutex g_tune_mu;
 
+// Tile variant forced for a pass kind (2 = P2, 3 = P3, 4 = P4) by ie_debug_force_tile; -1: autotuned.
+std::atomic<int> g_force_tile[5] = {{-1}, {-1}, {-1}, {-1}, {-1}};
+
 int tuned_variant(const TuneKey& k) {
+  if (k.kind >= 2 && k.kind <= 4) {
+    const int f = g_force_tile[k.kind].load();
+    if (f >= 0) return f;
+  }
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tuned.find(k);
   return it == g_tuned.end() ? -1 : it->second;
@@ -2317,6 +2324,14 @@ int32_t ie_tuned_tiles(char* buf, int32_t len) {
 }
 
 void ie_debug_fail_allocation(int32_t after) { g_alloc_fail_countdown.store(after < 0 ? -1 : after); }
+
+ie_status ie_debug_force_tile(int32_t pass, int32_t variant) {
+  if (pass < 2 || pass > 4) return IE_EINVAL;
+  const int nvar = pass == 3 ? kP3TileVariants : kTileVariants;
+  if (variant < -1 || variant >= nvar) return IE_EINVAL;
+  g_force_tile[pass].store(variant);
+  return IE_OK;
+}
 
 const char* ie_last_error(const ie_ctx* c) { return c ? c->err.c_str() : "null context"; }
 

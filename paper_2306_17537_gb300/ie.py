@@ -97,6 +97,7 @@ _SIGS = {
     "ie_tuned_tiles": (ct.c_int32, [ct.c_char_p, ct.c_int32]),
     "ie_last_error": (ct.c_char_p, [_P]),
     "ie_debug_fail_allocation": (None, [ct.c_int32]),
+    "ie_debug_force_tile": (ct.c_int32, [ct.c_int32, ct.c_int32]),
     "ie_destroy": (None, [_P]),
     # include/ie_fno.h
     "ie_fno_create": (ct.c_int, [ct.c_int32] * 9 + [ct.POINTER(_P)]),
@@ -460,6 +461,14 @@ def debug_fail_allocation(after: int):
     """ie_debug_fail_allocation: make the device allocation after `after` more successful ones report
     out-of-memory (testing hook; negative switches it off)."""
     _lib.ie_debug_fail_allocation(int(after))
+
+
+def debug_force_tile(pass_: int, variant: int):
+    """ie_debug_force_tile: run pass 2, 3 or 4 (P2, P3, P4) in the given tile variant in every later
+    convolution of this process (-1: back to the autotuner). Testing hook."""
+    st = _lib.ie_debug_force_tile(int(pass_), int(variant))
+    if st != IE_OK:
+        raise IEError(st, f"ie_debug_force_tile({pass_}, {variant})")
 
 
 def tuned_tiles() -> str:
