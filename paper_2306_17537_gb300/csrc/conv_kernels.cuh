@@ -37,9 +37,10 @@ template <typename T, int L, int NT = kThreads> struct LaneCfg {
 // ---------------------------------------------------------------- P1: J = dsigma x, x-FFT
 // CONTRACT: the contraction form, where ds holds dsigma M and mt holds M (both [6][...]); the kernel
 // then also stores w = M x (the field the epilogue of P5 subtracts the convolution from).
-// One component of J at a time: row p of the symmetric tensor times x, transformed and stored before the
-// next (x and the tensor rows are re-read from cache), so a thread holds one pencil of E values instead
-// of three.
+// Each cell's x, tensor (and M) are read once: J_x stays in registers for the first transform, while J_y
+// and J_z are parked in their own rows of A (the positions the transform later overwrites; the same
+// thread reads them back, and the lines are still in cache) and transformed one after the other, so a
+// thread holds one pencil of E values at a time.
 template <typename T, int L, bool CONTRACT>
 __global__ void __launch_bounds__(kThreads, 3) k_p1_contrast_fftx(
     const FieldC<T>* __restrict__ x, long x_cs, const FieldR<T>* __restrict__ ds, long d_cs,
@@ -52,39 +53,38 @@ __global__ void __launch_bounds__(kThreads, 3) k_p1_contrast_fftx(
   const long row = (long)blockIdx.x * P + p;
   const bool act = row < nrows;
   RowSM<T> sm{smem + p * RowSM<T>::words(L)};
-  if constexpr (CONTRACT) {  // w = M x
-    if (act) {
-#pragma unroll 4
-      for (int m = 0; m < E; ++m) {
-        const int i = t + TT * m;
-        if (i < nx) {
-          const long o = row * nx + i;
-          const FieldC<T> x0 = x[o], x1 = x[x_cs + o], x2 = x[2 * x_cs + o];
-          const R mxx = mt[o], myy = mt[d_cs + o], mzz = mt[2 * d_cs + o];
-          const R mxy = mt[3 * d_cs + o], mxz = mt[4 * d_cs + o], myz = mt[5 * d_cs + o];
-          w[o] = mk<R>(mxx * x0.x + mxy * x1.x + mxz * x2.x, mxx * x0.y + mxy * x1.y + mxz * x2.y);
-          w[w_cs + o] = mk<R>(mxy * x0.x + myy * x1.x + myz * x2.x, mxy * x0.y + myy * x1.y + myz * x2.y);
-          w[2 * w_cs + o] = mk<R>(mxz * x0.x + myz * x1.x + mzz * x2.x, mxz * x0.y + myz * x1.y + mzz * x2.y);
-        }
+  C<T> J[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int i = t + TT * m;
+    J[m] = czero<C<T>>();
+    if (act && i < nx) {
+      const long o = row * nx + i;
+      const FieldC<T> x0 = x[o], x1 = x[x_cs + o], x2 = x[2 * x_cs + o];
+      if constexpr (CONTRACT) {  // w = M x
+        const R mxx = mt[o], myy = mt[d_cs + o], mzz = mt[2 * d_cs + o];
+        const R mxy = mt[3 * d_cs + o], mxz = mt[4 * d_cs + o], myz = mt[5 * d_cs + o];
+        w[o] = mk<R>(mxx * x0.x + mxy * x1.x + mxz * x2.x, mxx * x0.y + mxy * x1.y + mxz * x2.y);
+        w[w_cs + o] = mk<R>(mxy * x0.x + myy * x1.x + myz * x2.x, mxy * x0.y + myy * x1.y + myz * x2.y);
+        w[2 * w_cs + o] = mk<R>(mxz * x0.x + myz * x1.x + mzz * x2.x, mxz * x0.y + myz * x1.y + mzz * x2.y);
       }
+      // (xx, yy, zz, xy, xz, yz) storage of the symmetric tensor
+      const R sxx = ds[o], syy = ds[d_cs + o], szz = ds[2 * d_cs + o];
+      const R sxy = ds[3 * d_cs + o], sxz = ds[4 * d_cs + o], syz = ds[5 * d_cs + o];
+      J[m] = to_c(mk<R>(sxx * x0.x + sxy * x1.x + sxz * x2.x, sxx * x0.y + sxy * x1.y + sxz * x2.y), T());
+      A[A_cs + row * L + i] =
+          to_c(mk<R>(sxy * x0.x + syy * x1.x + syz * x2.x, sxy * x0.y + syy * x1.y + syz * x2.y), T());
+      A[2 * A_cs + row * L + i] =
+          to_c(mk<R>(sxz * x0.x + syz * x1.x + szz * x2.x, sxz * x0.y + syz * x1.y + szz * x2.y), T());
     }
   }
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
-    // row c of the symmetric tensor in the (xx, yy, zz, xy, xz, yz) storage
-    const long k0 = (c == 0 ? 0 : c == 1 ? 3 : 4) * d_cs, k1 = (c == 0 ? 3 : c == 1 ? 1 : 5) * d_cs,
-               k2 = (c == 0 ? 4 : c == 1 ? 5 : 2) * d_cs;
-    C<T> J[E];
+    if (c > 0) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int i = t + TT * m;
-      if (act && i < nx) {
-        const long o = row * nx + i;
-        const FieldC<T> x0 = x[o], x1 = x[x_cs + o], x2 = x[2 * x_cs + o];
-        const R s0 = ds[k0 + o], s1 = ds[k1 + o], s2 = ds[k2 + o];
-        J[m] = to_c(mk<R>(s0 * x0.x + s1 * x1.x + s2 * x2.x, s0 * x0.y + s1 * x1.y + s2 * x2.y), T());
-      } else {
-        J[m] = czero<C<T>>();
+      for (int m = 0; m < E; ++m) {
+        const int i = t + TT * m;
+        J[m] = (act && i < nx) ? A[c * A_cs + row * L + i] : czero<C<T>>();
       }
     }
     pencil_fft<T, L, -1>(J, t, sm, tw);
