@@ -310,8 +310,9 @@ void ie_debug_fail_allocation(int32_t after);
  * tile variant `variant` (the numbering of ie_tuned_tiles) instead of the autotuned one; -1 returns the
  * pass to the autotuner. All variants compute bit-identical results, and this hook lets a test check
  * that. A z-pass variant that the arithmetic in use does not build (8 and 9 outside complex64) makes the
- * convolution fail with IE_ECUDA. IE_EINVAL for a pass or variant out of range. Not thread-safe with
- * respect to convolutions in flight on other threads. */
+ * convolution fail with IE_ECUDA. IE_EINVAL for a pass or variant out of range. The setting is a
+ * process-wide atomic; a convolution that another thread is already enqueuing may still use the
+ * previous choice. */
 ie_status ie_debug_force_tile(int32_t pass, int32_t variant);
 
 /* Last error message of the context (never NULL; "" when none). */
