@@ -11,7 +11,7 @@ outer iteration on the whole-grid system (the Krylov acceleration the paper prop
 on the contraction form of the operator, complex64 FFT convolution and Krylov vectors, FP64-accurate
 (double-float) whole-grid residuals. One step = one tool position's solve (incident field, DD solve,
 receivers); the model is uploaded (ie_set_contrast_dev / ie_set_contrast) at the first step of every
-round of 16 positions, inside the timed region. Green spectra (ie_create) depend only on grid, cell
+cycle of 16 positions, inside the timed region. Green spectra (ie_create) depend only on grid, cell
 size, background and frequency and are computed once before timing, as the paper precomputes them
 (Section 2.2). Inputs (fields 1.6 GB, Krylov bases tens of GB) are far larger than the 129 MB L2.
 
@@ -86,14 +86,14 @@ class BenchWorkload:
         return self.items[step % len(self.items)]
 
     def uploads_model(self, step: int) -> bool:
-        """The model is (re)uploaded at the first position of every round of positions."""
+        """The model is (re)uploaded at the first position of every cycle of positions."""
         return step % len(self.items) == 0
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=16, help="timed steps (default: one round of the 16 positions)")
+    ap.add_argument("--steps", type=int, default=16, help="timed steps (default: one cycle of the 16 tool positions)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--seed", type=int, default=0)
@@ -350,7 +350,7 @@ def run_gb300(args):
     H, _, st = results[-1]
     # ----------------------------------------------------------------- end to end (host buffers)
     # the same steps with every input from pinned host memory (the model at the first position of a
-    # round, sources and receivers every step) and the receiver fields back on the host every step
+    # cycle, sources and receivers every step) and the receiver fields back on the host every step
     s6_host = torch.from_numpy(np.ascontiguousarray(bw.sigma6)).pin_memory().numpy()
     h2d_total, d2h_total = 0, 0
 
