@@ -14,6 +14,8 @@
 #include "fft.cuh"
 #include "tma.cuh"
 
+#include <type_traits>
+
 namespace ie {
 
 constexpr int kThreads = 256;
@@ -236,79 +238,176 @@ __global__ void __launch_bounds__(P3Cfg<T, L, NT, MIR>::NTH, P3Cfg<T, L, NT, MIR
       }
     }
   }
-  // forward z-FFT of each component; spectrum left in spec[c] at the thread's own positions
-#pragma unroll 1
-  for (int c = 0; c < 3; ++c) {
-    LaneSM<T, WH> sm{col(c)};
-    if constexpr (kTma) {
-      if (!__syncthreads_and(mbar_wait(bar + c, 0))) {
-        if (t == 0 && w == 0) {
-          atomicExch(err, 1);
-          for (int c2 = c + 1; c2 < 3; ++c2) mbar_wait(bar + c2, 0);
+  if constexpr (std::is_same<T, df>::value) {
+    // forward z-FFT input of component c: false when a staging wait gave up (the block then ends)
+    auto load_input = [&](int c) -> bool {
+      if constexpr (kTma) {
+        if (!__syncthreads_and(mbar_wait(bar + c, 0))) {
+          if (t == 0 && w == 0) {
+            atomicExch(err, 1);
+            for (int c2 = c + 1; c2 < 3; ++c2) mbar_wait(bar + c2, 0);
+          }
+          return false;
         }
-        return;
+        // staged rows are dense; positions outside the source slab hold the copy's zero fill and are
+        // not read back (half of every pencil for the usual 2n padding)
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const int z = t + TT * m - os;
+          v[m] = (z >= 0 && z < nzs) ? col(c)[(t + TT * m) * WH] : czero<C<T>>();
+        }
+        __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]
+      } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const int z = t + TT * m - os;
+          v[m] = (act && z >= 0 && z < nzs) ? Bin[c * in_cs + z * plane + off] : czero<C<T>>();
+        }
       }
-      // staged rows are dense; positions outside the source slab hold the copy's zero fill and are
-      // not read back (half of every pencil for the usual 2n padding)
+      return true;
+    };
+    // Green product at the thread's own frequencies (no other thread touches these slots).
+    // The octant holds F[K_pq] for 0 <= k <= L/2 per axis; the full spectrum follows from the
+    // parities of K (diagonal components even, K_pq odd along p and q): with s_a = +-1 the side of
+    // axis a, F[K_pq](k) = s_p s_q F[K_pq](|k|), so Y_p = sum_q s_p s_q F_pq(|k|) J_q: the diagonal terms
+    // carry no sign and the off-diagonal ones the products s_x s_y, s_x s_z, s_y s_z. Register m of a
+    // pencil holds kz = t + TT*m, which lies in the lower half exactly when m < E/2 (the Nyquist
+    // frequency kz = L/2, where the odd components vanish, may take either side).
+    auto green_product = [&]() {
+      if (!act) return;
+      const int ox = Lx / 2 + 1, oy = Ly / 2 + 1;
+      const long ocs = (long)(L / 2 + 1) * oy * ox, ozs = (long)oy * ox;
+      const bool xlo = kx <= Lx / 2, ylo = ky <= Ly / 2;
+      const int ix = xlo ? kx : Lx - kx, iy = ylo ? ky : Ly - ky;
+      const bool nxy = xlo != ylo;
+      const C<T>* gb = G + (long)iy * ox + ix;
+      LaneSM<T, WH> s0{col(0)}, s1{col(1)}, s2{col(2)};
 #pragma unroll
       for (int m = 0; m < E; ++m) {
-        const int z = t + TT * m - os;
-        v[m] = (z >= 0 && z < nzs) ? col(c)[(t + TT * m) * WH] : czero<C<T>>();
+        const bool zlo = (E == 1) || (m < E / 2);  // lower half of kz: s_z = +1
+        const int kz = t + TT * m, iz = zlo ? kz : L - kz;
+        const bool nxz = zlo ? !xlo : xlo, nyz = zlo ? !ylo : ylo;
+        const C<T>* g = gb + iz * ozs;
+        const C<T> gxx = ldgv(g), gyy = ldgv(g + ocs), gzz = ldgv(g + 2 * ocs);
+        const C<T> gxy = ldgv(g + 3 * ocs), gxz = ldgv(g + 4 * ocs), gyz = ldgv(g + 5 * ocs);
+        const C<T> j0 = s0.ld(kz), j1 = s1.ld(kz), j2 = s2.ld(kz);
+        s0.st(kz, add_signed(add_signed(cmul(gxx, j0), nxy, cmul(gxy, j1)), nxz, cmul(gxz, j2)));
+        s1.st(kz, add_signed(add_signed(cmul(gyy, j1), nxy, cmul(gxy, j0)), nyz, cmul(gyz, j2)));
+        s2.st(kz, add_signed(add_signed(cmul(gzz, j2), nxz, cmul(gxz, j0)), nyz, cmul(gyz, j1)));
       }
+    };
+    // the spectrum of component c back into registers, for its inverse transform
+    auto load_spectrum = [&](const LaneSM<T, WH>& sm) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = sm.ld(t + TT * m);
       __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]
-    } else {
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int z = t + TT * m - os;
-        v[m] = (act && z >= 0 && z < nzs) ? Bin[c * in_cs + z * plane + off] : czero<C<T>>();
-      }
-    }
-    pencil_fft<T, L, -1>(v, t, sm, tw);
-#pragma unroll
-    for (int m = 0; m < E; ++m) sm.st(t + TT * m, v[m]);
-  }
-  // Green product at the thread's own frequencies (no other thread touches these slots).
-  // The octant holds F[K_pq] for 0 <= k <= L/2 per axis; the full spectrum follows from the
-  // parities of K (diagonal components even, K_pq odd along p and q): with s_a = +-1 the side of
-  // axis a, F[K_pq](k) = s_p s_q F[K_pq](|k|), so Y_p = sum_q s_p s_q F_pq(|k|) J_q: the diagonal terms
-  // carry no sign and the off-diagonal ones the products s_x s_y, s_x s_z, s_y s_z. Register m of a
-  // pencil holds kz = t + TT*m, which lies in the lower half exactly when m < E/2 (the Nyquist
-  // frequency kz = L/2, where the odd components vanish, may take either side).
-  if (act) {
-    const int ox = Lx / 2 + 1, oy = Ly / 2 + 1;
-    const long ocs = (long)(L / 2 + 1) * oy * ox, ozs = (long)oy * ox;
-    const bool xlo = kx <= Lx / 2, ylo = ky <= Ly / 2;
-    const int ix = xlo ? kx : Lx - kx, iy = ylo ? ky : Ly - ky;
-    const bool nxy = xlo != ylo;
-    const C<T>* gb = G + (long)iy * ox + ix;
-    LaneSM<T, WH> s0{col(0)}, s1{col(1)}, s2{col(2)};
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const bool zlo = (E == 1) || (m < E / 2);  // lower half of kz: s_z = +1
-      const int kz = t + TT * m, iz = zlo ? kz : L - kz;
-      const bool nxz = zlo ? !xlo : xlo, nyz = zlo ? !ylo : ylo;
-      const C<T>* g = gb + iz * ozs;
-      const C<T> gxx = ldgv(g), gyy = ldgv(g + ocs), gzz = ldgv(g + 2 * ocs);
-      const C<T> gxy = ldgv(g + 3 * ocs), gxz = ldgv(g + 4 * ocs), gyz = ldgv(g + 5 * ocs);
-      const C<T> j0 = s0.ld(kz), j1 = s1.ld(kz), j2 = s2.ld(kz);
-      s0.st(kz, add_signed(add_signed(cmul(gxx, j0), nxy, cmul(gxy, j1)), nxz, cmul(gxz, j2)));
-      s1.st(kz, add_signed(add_signed(cmul(gyy, j1), nxy, cmul(gxy, j0)), nyz, cmul(gyz, j2)));
-      s2.st(kz, add_signed(add_signed(cmul(gzz, j2), nxz, cmul(gxz, j0)), nyz, cmul(gyz, j1)));
-    }
-  }
-  // inverse z-FFT of each component and crop
-#pragma unroll 1
-  for (int c = 0; c < 3; ++c) {
-    LaneSM<T, WH> sm{col(c)};
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = sm.ld(t + TT * m);
-    __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]
-    pencil_fft<T, L, +1>(v, t, sm, tw);
-    if (act) {
+    };
+    // crop: the target slab's positions of the inverse transform
+    auto store_output = [&](int c) {
+      if (!act) return;
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const int z = t + TT * m - ot;
         if (z >= 0 && z < nzt) Bout[c * out_cs + z * plane + off] = v[m];
+      }
+    };
+    // double-float: the six transforms share one copy of the (large) unrolled FFT code, the direction
+    // given at run time, so that the kernel's code fits the instruction cache; the order of the work is
+    // the same as below (three forward transforms, the Green product, three inverse transforms)
+#pragma unroll 1
+    for (int pass = 0; pass < 6; ++pass) {
+      const bool fwd = pass < 3;
+      const int c = fwd ? pass : pass - 3;
+      if (pass == 3) green_product();
+      LaneSM<T, WH> sm{col(c)};
+      if (fwd) {
+        if (!load_input(c)) return;
+      } else {
+        load_spectrum(sm);
+      }
+      pencil_fft<T, L, kRuntimeSign>(v, t, sm, tw, fwd ? -1 : +1);
+      if (fwd) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) sm.st(t + TT * m, v[m]);
+      } else {
+        store_output(c);
+      }
+    }
+  } else {
+    // forward z-FFT of each component; spectrum left in spec[c] at the thread's own positions
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      LaneSM<T, WH> sm{col(c)};
+      if constexpr (kTma) {
+        if (!__syncthreads_and(mbar_wait(bar + c, 0))) {
+          if (t == 0 && w == 0) {
+            atomicExch(err, 1);
+            for (int c2 = c + 1; c2 < 3; ++c2) mbar_wait(bar + c2, 0);
+          }
+          return;
+        }
+        // staged rows are dense; positions outside the source slab hold the copy's zero fill and are
+        // not read back (half of every pencil for the usual 2n padding)
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const int z = t + TT * m - os;
+          v[m] = (z >= 0 && z < nzs) ? col(c)[(t + TT * m) * WH] : czero<C<T>>();
+        }
+        __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]
+      } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const int z = t + TT * m - os;
+          v[m] = (act && z >= 0 && z < nzs) ? Bin[c * in_cs + z * plane + off] : czero<C<T>>();
+        }
+      }
+      pencil_fft<T, L, -1>(v, t, sm, tw);
+#pragma unroll
+      for (int m = 0; m < E; ++m) sm.st(t + TT * m, v[m]);
+    }
+    // Green product at the thread's own frequencies (no other thread touches these slots).
+    // The octant holds F[K_pq] for 0 <= k <= L/2 per axis; the full spectrum follows from the
+    // parities of K (diagonal components even, K_pq odd along p and q): with s_a = +-1 the side of
+    // axis a, F[K_pq](k) = s_p s_q F[K_pq](|k|), so Y_p = sum_q s_p s_q F_pq(|k|) J_q: the diagonal terms
+    // carry no sign and the off-diagonal ones the products s_x s_y, s_x s_z, s_y s_z. Register m of a
+    // pencil holds kz = t + TT*m, which lies in the lower half exactly when m < E/2 (the Nyquist
+    // frequency kz = L/2, where the odd components vanish, may take either side).
+    if (act) {
+      const int ox = Lx / 2 + 1, oy = Ly / 2 + 1;
+      const long ocs = (long)(L / 2 + 1) * oy * ox, ozs = (long)oy * ox;
+      const bool xlo = kx <= Lx / 2, ylo = ky <= Ly / 2;
+      const int ix = xlo ? kx : Lx - kx, iy = ylo ? ky : Ly - ky;
+      const bool nxy = xlo != ylo;
+      const C<T>* gb = G + (long)iy * ox + ix;
+      LaneSM<T, WH> s0{col(0)}, s1{col(1)}, s2{col(2)};
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const bool zlo = (E == 1) || (m < E / 2);  // lower half of kz: s_z = +1
+        const int kz = t + TT * m, iz = zlo ? kz : L - kz;
+        const bool nxz = zlo ? !xlo : xlo, nyz = zlo ? !ylo : ylo;
+        const C<T>* g = gb + iz * ozs;
+        const C<T> gxx = ldgv(g), gyy = ldgv(g + ocs), gzz = ldgv(g + 2 * ocs);
+        const C<T> gxy = ldgv(g + 3 * ocs), gxz = ldgv(g + 4 * ocs), gyz = ldgv(g + 5 * ocs);
+        const C<T> j0 = s0.ld(kz), j1 = s1.ld(kz), j2 = s2.ld(kz);
+        s0.st(kz, add_signed(add_signed(cmul(gxx, j0), nxy, cmul(gxy, j1)), nxz, cmul(gxz, j2)));
+        s1.st(kz, add_signed(add_signed(cmul(gyy, j1), nxy, cmul(gxy, j0)), nyz, cmul(gyz, j2)));
+        s2.st(kz, add_signed(add_signed(cmul(gzz, j2), nxz, cmul(gxz, j0)), nyz, cmul(gyz, j1)));
+      }
+    }
+    // inverse z-FFT of each component and crop
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      LaneSM<T, WH> sm{col(c)};
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = sm.ld(t + TT * m);
+      __syncthreads();  // every thread holds its inputs before the exchanges overwrite spec[c]
+      pencil_fft<T, L, +1>(v, t, sm, tw);
+      if (act) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const int z = t + TT * m - ot;
+          if (z >= 0 && z < nzt) Bout[c * out_cs + z * plane + off] = v[m];
+        }
       }
     }
   }

@@ -26,11 +26,18 @@ template <typename T, int L> struct Plan {
   static constexpr int TT = L / E;                           // threads per pencil
 };
 
-// x * exp(SIGN * 2 pi i q / 16), q in [0, 8), with the trivial rotations done without multiplies.
-template <typename T, int SIGN> __device__ __forceinline__ C<T> rot16(int q, C<T> x) {
+// SIGN = -1 (forward) or +1 (inverse) fixes the direction at compile time; SIGN = 0 takes it from the
+// run-time argument sgn instead, so that one copy of the code serves both directions (used where the
+// unrolled transforms are large enough to miss the instruction cache).
+constexpr int kRuntimeSign = 0;
+
+// x * exp(s * 2 pi i q / 16), q in [0, 8), s = SIGN (or sgn), with the trivial rotations done without
+// multiplies.
+template <typename T, int SIGN> __device__ __forceinline__ C<T> rot16(int q, C<T> x, int sgn = SIGN) {
+  const int sg = SIGN != 0 ? SIGN : sgn;
   constexpr T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173, h = (T)0.70710678118654752440;
   if (q == 0) return x;
-  if (q == 4) return SIGN < 0 ? mk<T>(x.y, -x.x) : mk<T>(-x.y, x.x);
+  if (q == 4) return sg < 0 ? mk<T>(x.y, -x.x) : mk<T>(-x.y, x.x);
   T wr, wi;
   switch (q) {
     case 1: wr = c1; wi = s1; break;
@@ -40,33 +47,33 @@ template <typename T, int SIGN> __device__ __forceinline__ C<T> rot16(int q, C<T
     case 6: wr = -h; wi = h; break;
     default: wr = -c1; wi = s1; break;  // q == 7
   }
-  return cmul(x, mk<T>(wr, SIGN < 0 ? -wi : wi));
+  return cmul(x, mk<T>(wr, sg < 0 ? -wi : wi));
 }
 
 // In-place R-point DFT (R <= 16) on natural-order registers, radix-2 decimation in time.
 template <typename T, int R, int SIGN> struct DFT {
-  __device__ __forceinline__ static void run(C<T>* v) {
+  __device__ __forceinline__ static void run(C<T>* v, int sgn = SIGN) {
     C<T> e[R / 2], o[R / 2];
 #pragma unroll
     for (int i = 0; i < R / 2; ++i) {
       e[i] = v[2 * i];
       o[i] = v[2 * i + 1];
     }
-    DFT<T, R / 2, SIGN>::run(e);
-    DFT<T, R / 2, SIGN>::run(o);
+    DFT<T, R / 2, SIGN>::run(e, sgn);
+    DFT<T, R / 2, SIGN>::run(o, sgn);
 #pragma unroll
     for (int k = 0; k < R / 2; ++k) {
-      C<T> t = rot16<T, SIGN>(k * (16 / R), o[k]);
+      C<T> t = rot16<T, SIGN>(k * (16 / R), o[k], sgn);
       v[k] = e[k] + t;
       v[k + R / 2] = e[k] - t;
     }
   }
 };
 template <typename T, int SIGN> struct DFT<T, 1, SIGN> {
-  __device__ __forceinline__ static void run(C<T>*) {}
+  __device__ __forceinline__ static void run(C<T>*, int = SIGN) {}
 };
 template <typename T, int SIGN> struct DFT<T, 2, SIGN> {
-  __device__ __forceinline__ static void run(C<T>* v) {
+  __device__ __forceinline__ static void run(C<T>* v, int = SIGN) {
     C<T> a = v[0], b = v[1];
     v[0] = a + b;
     v[1] = a - b;
@@ -97,9 +104,9 @@ template <typename T, int W> struct LaneSM {
 };
 
 template <typename T, int SIGN>
-__device__ __forceinline__ C<T> twiddle(const C<T>* __restrict__ tw, int idx) {
+__device__ __forceinline__ C<T> twiddle(const C<T>* __restrict__ tw, int idx, int sgn = SIGN) {
   C<T> w = ldgv(tw + idx);
-  if (SIGN > 0) w.y = -w.y;
+  if ((SIGN != 0 ? SIGN : sgn) > 0) w.y = -w.y;
   return w;
 }
 
@@ -112,10 +119,11 @@ template <typename T> struct TwiddlePowers { static constexpr bool v = false; };
 template <> struct TwiddlePowers<float> { static constexpr bool v = true; };
 
 template <typename T, int R, int SIGN>
-__device__ __forceinline__ void butterfly_twiddles(const C<T>* __restrict__ tw, int q, C<T> (&p)[R]) {
+__device__ __forceinline__ void butterfly_twiddles(const C<T>* __restrict__ tw, int q, C<T> (&p)[R],
+                                                   int sgn = SIGN) {
   if constexpr (TwiddlePowers<T>::v) {
 #pragma unroll
-    for (int b = 1; b < R; b <<= 1) p[b] = twiddle<T, SIGN>(tw, q * b);
+    for (int b = 1; b < R; b <<= 1) p[b] = twiddle<T, SIGN>(tw, q * b, sgn);
 #pragma unroll
     for (int r = 3; r < R; ++r) {
       if (r & (r - 1)) {
@@ -126,7 +134,7 @@ __device__ __forceinline__ void butterfly_twiddles(const C<T>* __restrict__ tw, 
     }
   } else {
 #pragma unroll
-    for (int r = 1; r < R; ++r) p[r] = twiddle<T, SIGN>(tw, q * r);
+    for (int r = 1; r < R; ++r) p[r] = twiddle<T, SIGN>(tw, q * r, sgn);
   }
 }
 
@@ -139,7 +147,8 @@ template <typename T, int L, int SIGN, int NS, class SM> struct Stages {
   static constexpr bool FIRST = (NS == 1);
   static constexpr bool LAST = (NS * R == L);
 
-  __device__ __forceinline__ static void run(C<T> (&v)[E], int t, const SM& sm, const C<T>* __restrict__ tw) {
+  __device__ __forceinline__ static void run(C<T> (&v)[E], int t, const SM& sm, const C<T>* __restrict__ tw,
+                                             int sgn = SIGN) {
     C<T> x[NB][R];
     if constexpr (FIRST) {
 #pragma unroll
@@ -157,11 +166,11 @@ template <typename T, int L, int SIGN, int NS, class SM> struct Stages {
         const int j = t + TT * b;
         const int k = j & (NS - 1);
         C<T> p[R];
-        butterfly_twiddles<T, R, SIGN>(tw, k * (TWN / (NS * R)), p);
+        butterfly_twiddles<T, R, SIGN>(tw, k * (TWN / (NS * R)), p, sgn);
 #pragma unroll
         for (int r = 1; r < R; ++r) x[b][r] = cmul(x[b][r], p[r]);
       }
-      DFT<T, R, SIGN>::run(x[b]);
+      DFT<T, R, SIGN>::run(x[b], sgn);
     }
     if constexpr (LAST) {
 #pragma unroll
@@ -178,17 +187,18 @@ template <typename T, int L, int SIGN, int NS, class SM> struct Stages {
         for (int r = 0; r < R; ++r) sm.st(base + r * NS, x[b][r]);
       }
       __syncthreads();
-      Stages<T, L, SIGN, (LAST ? NS : NS * R), SM>::run(v, t, sm, tw);
+      Stages<T, L, SIGN, (LAST ? NS : NS * R), SM>::run(v, t, sm, tw, sgn);
     }
   }
 };
 
-// Forward (SIGN = -1) or unnormalised inverse (SIGN = +1) DFT of one pencil held as described above.
-// Every thread of the block must call it (it contains __syncthreads when L > E).
+// Forward (SIGN = -1) or unnormalised inverse (SIGN = +1) DFT of one pencil held as described above;
+// SIGN = kRuntimeSign takes the direction from sgn. Every thread of the block must call it (it contains
+// __syncthreads when L > E).
 template <typename T, int L, int SIGN, class SM>
 __device__ __forceinline__ void pencil_fft(C<T> (&v)[Plan<T, L>::E], int t, const SM& sm,
-                                           const C<T>* __restrict__ tw) {
-  Stages<T, L, SIGN, 1, SM>::run(v, t, sm, tw);
+                                           const C<T>* __restrict__ tw, int sgn = SIGN) {
+  Stages<T, L, SIGN, 1, SM>::run(v, t, sm, tw, sgn);
 }
 
 }  // namespace ie
